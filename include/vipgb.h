@@ -1,0 +1,255 @@
+/*
+ * vipgb.h - C ABI of libvipgb: the data-parallel hot path of variational
+ * Bayesian full-waveform inversion (Zhang & Curtis, "VIP - Variational
+ * Inversion Package", arXiv 2310.13325) on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers unless marked "host".
+ *  - The caller owns every buffer it passes; the library never frees them.
+ *    An fwi_ctx owns only its scratch memory, CUDA graphs and tuning cache.
+ *  - Arrays are row-major with the last index fastest. A velocity model
+ *    v[nz][nx] has x (horizontal) fastest; particle sets are X[n][d] with
+ *    d = nz * nx.
+ *  - Calls are asynchronous and ordered on the given stream (NULL = legacy
+ *    default stream) unless stated otherwise. A return of VIP_OK means the
+ *    work was enqueued; a negative return is an error code and nothing was
+ *    enqueued unless stated otherwise. vip_strerror() names each code.
+ *  - Units: velocity m/s, grid spacing m, time s.
+ */
+#ifndef VIPGB_H
+#define VIPGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *vip_stream_t; /* same type as cudaStream_t */
+
+/* ---- status codes ---------------------------------------------------- */
+#define VIP_OK            0
+#define VIP_ERR_ARG      -1  /* invalid argument (shape, pointer, range)     */
+#define VIP_ERR_CFL      -2  /* max(v) dt / dx above the 8th-order limit     */
+#define VIP_ERR_NOMEM    -3  /* workspace too small / device allocation fail */
+#define VIP_ERR_CUDA     -4  /* a CUDA runtime call failed                  */
+#define VIP_ERR_TIMEOUT  -5  /* a bounded device-side wait gave up          */
+#define VIP_ERR_NOTPD    -6  /* kernel matrix not positive definite          */
+#define VIP_ERR_UNSUPPORTED -7 /* no feasible launch plan on this device      */
+
+const char *vip_strerror(int code);
+
+/* Text of the first CUDA runtime failure recorded on the calling host
+ * thread since the last vip_clear_error() ("" if none). Diagnostics only. */
+const char *vip_last_error(void);
+void vip_clear_error(void);
+
+/* ======================================================================
+ * Full-waveform inversion forward / adjoint (paper Sec. 3 and Sec. 4.2)
+ *
+ * The paper simulates data with "a time-domain finite difference method"
+ * and a 10 Hz Ricker wavelet and obtains velocity gradients "using the
+ * adjoint method" (Sec. 4.2); the scheme is fixed here as
+ *   a^{n+1} = g [2 a^n + w (L a^n + s^n)] - g^2 a^{n-1},  w = vpad^2 dt^2,
+ * L the 8th-order 5-arm Laplacian with zero values outside the padded grid,
+ * vpad the model edge-replicated into an nsponge-cell sponge on all sides,
+ * g the Cerjan taper exp(-(alpha*i)^2) exp(-(alpha*j)^2) (i, j = cells into
+ * the sponge), s^n = f(n dt)/dx^2 at the source node with the Ricker
+ * f(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), and the trace
+ * sample d[r][n] = a^{n+1} at receiver r (n = 0 .. nt-1).
+ * The misfit is the negative log of the Gaussian likelihood (Eq. 26),
+ *   J = 1/2 sum_{s,r,n} ((d - d_obs) / sigma)^2,
+ * and gradients are those of the exact discrete adjoint of the recurrence,
+ * folded from the padded grid onto the physical cells.
+ * ====================================================================== */
+
+typedef struct {
+    int   nz, nx;          /* physical grid                                  */
+    float dx;              /* grid spacing (m), square cells                 */
+    float dt;              /* time step (s)                                  */
+    int   nt;              /* number of time steps = samples per trace       */
+    int   nsponge;         /* sponge width in cells (20)                     */
+    float sponge_alpha;    /* Cerjan decay constant (0.015)                  */
+    float f0;              /* Ricker peak frequency (Hz)                     */
+    float t0;              /* Ricker delay (s); <= 0 selects 1/f0            */
+    int   nsrc;            /* number of sources S                            */
+    const int *src_iz;     /* host [S] physical row of each source           */
+    const int *src_ix;     /* host [S] physical column of each source        */
+    int   nrec;            /* number of receivers R                          */
+    const int *rec_iz;     /* host [R] physical row of each receiver         */
+    const int *rec_ix;     /* host [R] physical column of each receiver      */
+} fwi_geom;
+
+typedef struct fwi_ctx fwi_ctx;
+
+/* Precision of the stored forward wavefield snapshots that the imaging
+ * condition reads back during the adjoint sweep. The stencil itself always
+ * runs in FP32; restart checkpoints (checkpoint interval > 1) are FP32. */
+#define FWI_FP32       0
+#define FWI_CKPT_BF16  1
+#define FWI_CKPT_FP16  2   /* FP16 with a power-of-two scale per 128 cells */
+
+/* Execution modes. BATCHED: every (particle, source) pair of a call runs in
+ * one persistent thread-block-cluster launch that keeps the wavefields in
+ * shared memory for all time steps (replayed from a CUDA graph).
+ * PLAIN: one (particle, source) pair at a time, one kernel launch per time
+ * step, wavefields in global memory, no graph - the comparison baseline. */
+#define FWI_MODE_BATCHED 0
+#define FWI_MODE_PLAIN   1
+
+/* Create a context for one acquisition geometry. Copies *geom (and the host
+ * index arrays). workspace_limit_bytes caps the device scratch the context
+ * may allocate (0 = 85% of free device memory at each call).
+ * Errors: VIP_ERR_ARG (bad sizes, indices outside the physical grid,
+ * duplicate receiver cells), VIP_ERR_CUDA. Synchronous. */
+int  fwi_create(const fwi_geom *geom, size_t workspace_limit_bytes,
+                fwi_ctx **out);
+void fwi_destroy(fwi_ctx *ctx);
+
+/* Select the execution mode (FWI_MODE_*) and the restart-checkpoint interval
+ * K (1 = store every snapshot, no recomputation; K > 1 = store the state
+ * every K steps and recompute each K-step segment during the adjoint sweep;
+ * 0 = choose automatically from the workspace limit). */
+int  fwi_set_mode(fwi_ctx *ctx, int mode, int ckpt_every);
+
+/* Autotuning of the batched launch (cluster size, rows per thread, threads
+ * per block). When enabled, the first batched call with a new (P, mode,
+ * precision) times short runs (48 steps, one wave of clusters) of the
+ * candidate launches on the caller's own inputs, synchronously, and caches
+ * the fastest in the context; later calls reuse it. Without tuning a cost
+ * model picks the launch. fwi_autotune(ctx, P, precision) enables tuning. */
+int  fwi_autotune(fwi_ctx *ctx, int P, int precision);
+
+/* Force the batched launch shape: Q CTAs per cluster (1..16), V rows per
+ * thread (4 or 8, 0 = any) and T threads per CTA (multiple of 32, 0 = any);
+ * Q = 0 restores automatic choice. A shape that does not fit the device
+ * makes later calls return VIP_ERR_UNSUPPORTED. Results do not depend on
+ * the shape: every cell update is evaluated identically. */
+int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T);
+int  fwi_set_autotune(fwi_ctx *ctx, int enable);
+
+/* Describe the plan chosen for P particles: writes up to 8 ints to plan_out
+ * (host): {cluster_ctas, rows_per_thread, threads, band_rows, concurrent
+ * pairs, ckpt_every, work_items, sources_per_item}, and the device bytes
+ * the context holds after planning to bytes_out (host, may be NULL). */
+int  fwi_query_plan(fwi_ctx *ctx, int P, int precision, int *plan_out,
+                    size_t *bytes_out);
+
+/* Seismograms for P models.
+ *   v    [P][nz][nx] velocities (m/s)
+ *   seis [P][S][R][nt] output traces
+ * Errors: VIP_ERR_ARG, VIP_ERR_NOMEM, VIP_ERR_CUDA. The stability bound is
+ * checked on the device and reported by fwi_last_status(). */
+int  fwi_forward(fwi_ctx *ctx, const float *v, int P, float *seis,
+                 vip_stream_t stream);
+
+/* Misfit and its velocity gradient for P models (the data-parallel hot path).
+ *   v      [P][nz][nx] velocities
+ *   dobs   [S][R][nt] observed traces
+ *   sigma  scalar data standard deviation (Eq. 26 with sigma_i = sigma)
+ *   misfit [P] output, J per model, accumulated in FP64
+ *   grad   [P][nz][nx] output dJ/dv (J >= 0; grad log p = -grad inside the
+ *          uniform prior's bounds)
+ *   precision FWI_FP32 | FWI_CKPT_BF16 | FWI_CKPT_FP16 */
+int  fwi_gradient(fwi_ctx *ctx, const float *v, int P, const float *dobs,
+                  float sigma, double *misfit, float *grad, int precision,
+                  vip_stream_t stream);
+
+/* Backward of the seismogram map (the autograd rule of fwi_forward):
+ *   dseis [P][S][R][nt] upstream sensitivity dL/dseis
+ *   grad  [P][nz][nx]   output dL/dv */
+int  fwi_adjoint(fwi_ctx *ctx, const float *v, int P, const float *dseis,
+                 float *grad, int precision, vip_stream_t stream);
+
+/* Device-side status of the last call on this context (synchronises the
+ * stream it last used): VIP_OK, VIP_ERR_CFL if some model violated
+ * max(v) dt/dx <= 0.5547 (the 2-D stability bound of the 8th-order
+ * leapfrog scheme), in which case the outputs of that call are undefined. */
+int  fwi_last_status(fwi_ctx *ctx);
+
+/* ======================================================================
+ * SVGD, Eq. (13)-(17):
+ *   phi(m_i) = 1/n sum_j [k(m_j, m_i) G_j + k(m_j, m_i) (m_i - m_j) / h^2],
+ *   m_i <- clip(m_i + eps phi(m_i), lo, hi)
+ * with the RBF kernel of Eq. (16), k = exp(-|m - m'|^2 / (2 h^2)). The paper
+ * leaves h free ("a scale factor"); h2 <= 0 selects the median rule
+ *   h^2 = med / (2 ln(n + 1)),
+ * med the median of all n^2 squared distances (zero diagonal included, mean
+ * of the two middle values for even n^2; h^2 = 1 if med < 1e-30). The bound
+ * reset is the paper's first uniform-prior strategy (Sec. 3).
+ *   X   [n][d] particles, updated in place
+ *   G   [n][d] gradient at each particle; grad log p = gscale * G (pass
+ *       gscale = 1 for log-posterior gradients, -1 for the misfit gradients
+ *       dJ/dv of fwi_gradient: inside a uniform prior's box grad log p = -dJ/dv)
+ *   lo, hi [d] per-coordinate bounds, or NULL for none
+ *   gram_precision: how |m_i - m_j|^2 is formed (VIP_GRAM_*)
+ *   ws, ws_bytes: caller scratch of at least svgd_workspace_size() bytes,
+ *           256-byte aligned
+ *   h2_used [1] device double, the bandwidth used (may be NULL)
+ * ====================================================================== */
+#define VIP_GRAM_BF16    0  /* one BF16 tensor-core Gram, FP32 accumulate  */
+#define VIP_GRAM_BF16X3  1  /* hi/lo BF16 split, three tensor-core products */
+#define VIP_GRAM_FP32    2  /* SIMT FP32 Gram without tensor cores (reference) */
+
+size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic);
+
+/* Rows a9-a10 of one step on their own: the centred Gram on the tensor cores
+ * (or SIMT), the squared distances D2 [n][n] (device, FP64, zero diagonal,
+ * clamped at 0) and the median bandwidth h2_used [1] (device double, as in
+ * svgd_step with h2 <= 0). ws as for svgd_step (stochastic = 0). */
+int  svgd_sqdist(const float *X, int n, int d, int gram_precision, double *D2,
+                 double *h2_used, void *ws, size_t ws_bytes, vip_stream_t stream);
+
+int  svgd_step(float *X, const float *G, float gscale, int n, int d, float eps,
+               float h2, const float *lo, const float *hi, int gram_precision,
+               void *ws, size_t ws_bytes, double *h2_used,
+               vip_stream_t stream);
+
+/* Stochastic SVGD, Eq. (22) with the noise of Eq. (25):
+ *   m_i <- clip(m_i + eps phi(m_i) + sqrt(2 eps / n) sum_j Lk_ij xi_j, lo, hi),
+ * Lk the lower Cholesky factor of Kbar + tau I (Kbar_ij = k(m_i, m_j),
+ * tau = 1e-6 n, multiplied by 10 on failure, at most 3 retries; the factor
+ * is FP32). xi [n][d] is either the caller's standard-normal array or, when
+ * xi == NULL, drawn on the device from Philox-4x32-10 keyed by (seed, iter)
+ * (counter = (column/4, row, iter)). tau_used [1] device double (may be
+ * NULL). Synchronises the stream once to read the factorisation status.
+ * Errors: as svgd_step, VIP_ERR_NOTPD if every retry failed. */
+int  ssvgd_step(float *X, const float *G, float gscale, int n, int d, float eps,
+                float h2, const float *lo, const float *hi, int gram_precision,
+                void *ws, size_t ws_bytes, double *h2_used,
+                uint64_t seed, uint64_t iter, const float *xi,
+                double *tau_used, vip_stream_t stream);
+
+/* ======================================================================
+ * Mean-field ADVI (Eq. 7-12 with a diagonal Cholesky factor, Sec. 5):
+ * theta = mu + e^omega * eta, m = T^{-1}(theta) with the logit transform of
+ * Eq. (12) when a, b are given (identity when a == b == NULL).
+ * ====================================================================== */
+
+/* m_out[s][i] = T^{-1}(mu_i + e^{omega_i} eta[s][i]) for S samples. */
+int  advi_sample(const float *mu, const float *omega, const float *eta,
+                 int S, int d, const float *a, const float *b, float *m_out,
+                 vip_stream_t stream);
+
+/* One ELBO ascent step (Eq. 10-11 on the diagonal) with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8):
+ *   g_s = gm[s] dm/dtheta + d log|det J|/dtheta,
+ *   grad_mu = mean_s g_s, grad_omega = mean_s g_s eta_s e^omega + 1.
+ *   adam_state [4][d]: first and second moments of mu, then of omega,
+ *              zero before the first step; t >= 1 the step number.
+ *   gm [S][d] d log p / dm at m_s = advi_sample(...). */
+int  advi_step(float *mu, float *omega, float *adam_state, int t,
+               const float *eta, const float *gm, int S, int d,
+               const float *a, const float *b, float lr,
+               vip_stream_t stream);
+
+/* Standard normals out[rows][cols] from the Philox-4x32-10 stream used by
+ * ssvgd_step (same counter layout), for the ADVI draws eta. */
+int  vip_philox_normal(float *out, int rows, int cols, uint64_t seed,
+                       uint64_t iter, vip_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIPGB_H */

@@ -1,0 +1,305 @@
+"""GB300-native hot path of variational Bayesian full-waveform inversion.
+
+Thin Python layer over libvipgb (include/vipgb.h): argument checking and
+marshalling of torch CUDA tensors into the C ABI. Every step of the
+computation runs in the library's CUDA kernels; there is no CPU fallback -
+calls fail loudly when the library is missing or a tensor is not on a GPU.
+
+Entry points follow the paper (Zhang & Curtis, arXiv 2310.13325):
+  Fwi.forward / Fwi.gradient / Fwi.adjoint   wave simulation, Gaussian misfit
+                                             (Eq. 26), adjoint-state gradient
+  FwiSeis                                    torch.autograd.Function of the
+                                             seismogram map
+  svgd_step (Eq. 17), ssvgd_step (Eq. 22, 25), advi_sample / advi_step
+  (Eq. 10-12, mean-field), philox_normal
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FwiGeom, VipError, check
+
+FWI_FP32, FWI_CKPT_BF16, FWI_CKPT_FP16 = 0, 1, 2
+FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
+VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
+
+__all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "advi_sample", "advi_step",
+           "philox_normal", "svgd_workspace_size", "svgd_sqdist", "FWI_FP32", "FWI_CKPT_BF16",
+           "FWI_CKPT_FP16", "FWI_MODE_BATCHED", "FWI_MODE_PLAIN", "VIP_GRAM_BF16",
+           "VIP_GRAM_BF16X3", "VIP_GRAM_FP32", "VipError"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Fwi:
+    """FWI context for one acquisition geometry (wraps fwi_create)."""
+
+    def __init__(self, nz, nx, dx, dt, nt, src_iz, src_ix, rec_iz, rec_ix, f0=10.0,
+                 t0=0.0, nsponge=20, sponge_alpha=0.015, workspace_limit=0):
+        L = _lib.load()
+        self.nz, self.nx, self.nt = int(nz), int(nx), int(nt)
+        self._arrays = [np.ascontiguousarray(a, dtype=np.int32)
+                        for a in (src_iz, src_ix, rec_iz, rec_ix)]
+        self.S = self._arrays[0].size
+        self.R = self._arrays[2].size
+        cp = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for a in self._arrays]
+        g = FwiGeom(self.nz, self.nx, float(dx), float(dt), self.nt, int(nsponge),
+                    float(sponge_alpha), float(f0), float(t0), self.S, cp[0], cp[1],
+                    self.R, cp[2], cp[3])
+        h = ctypes.c_void_p()
+        check(L.fwi_create(ctypes.byref(g), int(workspace_limit), ctypes.byref(h)),
+              "fwi_create")
+        self._h = h
+        self._L = L
+
+    @classmethod
+    def from_config(cls, cfg, geo, **kw):
+        return cls(cfg.nz, cfg.nx, cfg.dx, cfg.dt, cfg.nt, geo["src_iz"], geo["src_ix"],
+                   geo["rec_iz"], geo["rec_ix"], f0=cfg.f0, nsponge=cfg.nsponge,
+                   sponge_alpha=cfg.sponge_alpha, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.fwi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mode(self, mode=FWI_MODE_BATCHED, ckpt_every=1):
+        check(self._L.fwi_set_mode(self._h, int(mode), int(ckpt_every)), "fwi_set_mode")
+
+    def set_plan(self, Q=0, V=0, T=0):
+        """Force the batched launch shape (cluster CTAs, rows per thread,
+        threads per CTA); Q=0 returns to automatic choice."""
+        check(self._L.fwi_set_plan(self._h, int(Q), int(V), int(T)), "fwi_set_plan")
+
+    def set_autotune(self, enable=True):
+        check(self._L.fwi_set_autotune(self._h, int(bool(enable))), "fwi_set_autotune")
+
+    def query_plan(self, P, precision=FWI_FP32):
+        out = (ctypes.c_int * 8)()
+        nb = ctypes.c_size_t()
+        check(self._L.fwi_query_plan(self._h, int(P), int(precision), out,
+                                     ctypes.byref(nb)), "fwi_query_plan")
+        keys = ("cluster_ctas", "rows_per_thread", "threads", "band_rows",
+                "concurrent_pairs", "ckpt_every", "work_items", "sources_per_item")
+        d = dict(zip(keys, list(out)))
+        d["scratch_bytes"] = nb.value
+        return d
+
+    def last_status(self):
+        return self._L.fwi_last_status(self._h)
+
+    def _models(self, v):
+        torch = _torch()
+        if v.dim() == 2:
+            v = v.unsqueeze(0)
+        if tuple(v.shape[1:]) != (self.nz, self.nx) and v.shape[-1] != self.nz * self.nx:
+            raise ValueError("models must be [P, nz, nx] or [P, nz*nx]")
+        return v.reshape(v.shape[0], self.nz, self.nx).contiguous(), v.shape[0]
+
+    def forward(self, v, out=None, stream=None):
+        torch = _torch()
+        v, P = self._models(v)
+        if out is None:
+            out = torch.empty((P, self.S, self.R, self.nt), device=v.device,
+                              dtype=torch.float32)
+        check(self._L.fwi_forward(self._h, _ptr(v, torch.float32, "v"), P,
+                                  _ptr(out, torch.float32, "seis"), _stream(stream)),
+              "fwi_forward")
+        return out
+
+    def gradient(self, v, dobs, sigma, precision=FWI_FP32, misfit=None, grad=None,
+                 stream=None):
+        """Returns (misfit [P] float64, dJ/dv [P, nz, nx])."""
+        torch = _torch()
+        v, P = self._models(v)
+        if misfit is None:
+            misfit = torch.empty(P, device=v.device, dtype=torch.float64)
+        if grad is None:
+            grad = torch.empty((P, self.nz, self.nx), device=v.device, dtype=torch.float32)
+        if tuple(dobs.shape) != (self.S, self.R, self.nt):
+            raise ValueError("dobs must be [S, R, nt]")
+        check(self._L.fwi_gradient(self._h, _ptr(v, torch.float32, "v"), P,
+                                   _ptr(dobs, torch.float32, "dobs"), float(sigma),
+                                   _ptr(misfit, torch.float64, "misfit"),
+                                   _ptr(grad, torch.float32, "grad"), int(precision),
+                                   _stream(stream)), "fwi_gradient")
+        return misfit, grad
+
+    def adjoint(self, v, dseis, precision=FWI_FP32, grad=None, stream=None):
+        torch = _torch()
+        v, P = self._models(v)
+        if grad is None:
+            grad = torch.empty((P, self.nz, self.nx), device=v.device, dtype=torch.float32)
+        if tuple(dseis.shape) != (P, self.S, self.R, self.nt):
+            raise ValueError("dseis must be [P, S, R, nt]")
+        check(self._L.fwi_adjoint(self._h, _ptr(v, torch.float32, "v"), P,
+                                  _ptr(dseis.contiguous(), torch.float32, "dseis"),
+                                  _ptr(grad, torch.float32, "grad"), int(precision),
+                                  _stream(stream)), "fwi_adjoint")
+        return grad
+
+
+def _make_fwiseis():
+    torch = _torch()
+
+    class FwiSeis(torch.autograd.Function):
+        """Seismograms as a differentiable function of the velocity models:
+        forward = fwi_forward, backward = fwi_adjoint (exact discrete adjoint)."""
+
+        @staticmethod
+        def forward(ctx, v, fwi):
+            ctx.fwi = fwi
+            ctx.save_for_backward(v)
+            return fwi.forward(v.detach())
+
+        @staticmethod
+        def backward(ctx, gseis):
+            (v,) = ctx.saved_tensors
+            g = ctx.fwi.adjoint(v.detach(), gseis.contiguous())
+            return g.reshape(v.shape), None
+
+    return FwiSeis
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_fwiseis()
+        return getattr(_Lazy._cls, name)
+
+
+FwiSeis = _Lazy()
+
+
+def svgd_workspace_size(n, d, gram_precision=VIP_GRAM_BF16X3, stochastic=False):
+    return int(_lib.load().svgd_workspace_size(int(n), int(d), int(gram_precision),
+                                               int(bool(stochastic))))
+
+
+def _workspace(n, d, gram_precision, stochastic, ws, device):
+    torch = _torch()
+    need = svgd_workspace_size(n, d, gram_precision, stochastic)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=device)
+    return ws
+
+
+def svgd_sqdist(X, gram_precision=VIP_GRAM_BF16X3, ws=None, stream=None):
+    """Squared pairwise distances D2 [n, n] (float64) of the particles X [n, d]
+    and the median bandwidth h^2 (device float64 [1])."""
+    torch = _torch()
+    n, d = X.shape
+    ws = _workspace(n, d, gram_precision, False, ws, X.device)
+    D2 = torch.empty((n, n), dtype=torch.float64, device=X.device)
+    h2 = torch.empty(1, dtype=torch.float64, device=X.device)
+    check(_lib.load().svgd_sqdist(_ptr(X, torch.float32, "X"), n, d, int(gram_precision),
+                                  _ptr(D2, torch.float64), _ptr(h2, torch.float64), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "svgd_sqdist")
+    return D2, h2
+
+
+def svgd_step(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GRAM_BF16X3,
+              ws=None, h2_used=None, gscale=1.0, stream=None):
+    """In-place SVGD update of X [n, d] (Eq. 17) with grad log p = gscale * G.
+    Returns the workspace tensor (reusable) and h2_used (device float64 [1])."""
+    torch = _torch()
+    n, d = X.shape
+    ws = _workspace(n, d, gram_precision, False, ws, X.device)
+    if h2_used is None:
+        h2_used = torch.empty(1, dtype=torch.float64, device=X.device)
+    check(_lib.load().svgd_step(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
+                                float(gscale), n, d, float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
+                                _ptr(hi, torch.float32, "hi"), int(gram_precision),
+                                _ptr(ws), ws.numel(), _ptr(h2_used, torch.float64),
+                                _stream(stream)), "svgd_step")
+    return ws, h2_used
+
+
+def ssvgd_step(X, G, eps, seed, it, xi=None, h2=0.0, lo=None, hi=None,
+               gram_precision=VIP_GRAM_BF16X3, ws=None, h2_used=None, tau_used=None,
+               gscale=1.0, stream=None):
+    """In-place stochastic SVGD update of X [n, d] (Eq. 22 with the noise of
+    Eq. 25); xi None draws the noise from Philox(seed, it) on the device."""
+    torch = _torch()
+    n, d = X.shape
+    ws = _workspace(n, d, gram_precision, True, ws, X.device)
+    if h2_used is None:
+        h2_used = torch.empty(1, dtype=torch.float64, device=X.device)
+    if tau_used is None:
+        tau_used = torch.empty(1, dtype=torch.float64, device=X.device)
+    check(_lib.load().ssvgd_step(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
+                                 float(gscale), n, d, float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
+                                 _ptr(hi, torch.float32, "hi"), int(gram_precision),
+                                 _ptr(ws), ws.numel(), _ptr(h2_used, torch.float64),
+                                 int(seed), int(it), _ptr(xi, torch.float32, "xi"),
+                                 _ptr(tau_used, torch.float64), _stream(stream)),
+          "ssvgd_step")
+    return ws, h2_used, tau_used
+
+
+def advi_sample(mu, omega, eta, a=None, b=None, out=None, stream=None):
+    torch = _torch()
+    S, d = eta.shape
+    if out is None:
+        out = torch.empty((S, d), dtype=torch.float32, device=mu.device)
+    check(_lib.load().advi_sample(_ptr(mu, torch.float32, "mu"),
+                                  _ptr(omega, torch.float32, "omega"),
+                                  _ptr(eta, torch.float32, "eta"), S, d,
+                                  _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                  _ptr(out, torch.float32, "m_out"), _stream(stream)),
+          "advi_sample")
+    return out
+
+
+def advi_step(mu, omega, adam_state, t, eta, gm, lr, a=None, b=None, stream=None):
+    """In-place Adam ascent of (mu, omega); adam_state [4, d] zero-initialised."""
+    torch = _torch()
+    S, d = eta.shape
+    check(_lib.load().advi_step(_ptr(mu, torch.float32, "mu"),
+                                _ptr(omega, torch.float32, "omega"),
+                                _ptr(adam_state, torch.float32, "adam_state"), int(t),
+                                _ptr(eta, torch.float32, "eta"), _ptr(gm, torch.float32, "gm"),
+                                S, d, _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                float(lr), _stream(stream)), "advi_step")
+
+
+def philox_normal(rows, cols, seed, it, out=None, device="cuda"):
+    torch = _torch()
+    if out is None:
+        out = torch.empty((rows, cols), dtype=torch.float32, device=device)
+    check(_lib.load().vip_philox_normal(_ptr(out, torch.float32, "out"), int(rows),
+                                        int(cols), int(seed), int(it), _stream()),
+          "vip_philox_normal")
+    return out

@@ -1,0 +1,302 @@
+// tcgen05 Gram kernel for sm_103a.
+//
+// One CTA of 4 warps computes one 128x128 FP32 tile of Xc Xc^T over a range
+// of 64-wide coordinate blocks:
+//   - thread 0 issues TMA tile loads (128 rows x 64 BF16 = 128 B per row,
+//     128-byte swizzle) of the row block i and the row block j into a
+//     3-stage shared-memory ring, signalling a "full" mbarrier per stage;
+//   - thread 32 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M=128,
+//     N=128, K=16, both operands K-major) into a 128-column TMEM accumulator
+//     and releases each stage with tcgen05.commit on its "empty" mbarrier;
+//   - after the last block all four warps read the accumulator back with
+//     tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and store
+//     the partial tile.
+// Every mbarrier wait is bounded (about one second of clock cycles); on
+// expiry the kernel records bit 0 in *err, skips its remaining work, waits
+// for its outstanding copies with the same bound, frees TMEM and returns.
+#include "gram.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace vip {
+
+constexpr int GT_STAGES = 3;
+constexpr int GT_TILE_BYTES = 128 * 64 * 2;           // one operand tile
+constexpr int GT_STAGE_BYTES = 2 * GT_TILE_BYTES;     // A and B
+constexpr long long GT_WAIT_CYCLES = 2000000000ll;    // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and flags *err) when the bound expires.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity)) {
+    if (clock64() - t0 > GT_WAIT_CYCLES) {
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle: rows of 128 B, 8-row (1024 B) swizzle atoms stacked along
+// M/N (stride byte offset 1024), leading byte offset unused for this layout,
+// descriptor version 1, layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N>>3 at bits
+// 17-22, M>>4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap mh,
+                                                         const __grid_constant__ CUtensorMap ml,
+                                                         int KB, int kper, int total, int np,
+                                                         float *parts, int *err) {
+  extern __shared__ __align__(1024) uint8_t gsm_raw[];
+  // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
+  uint8_t *ring = (uint8_t *)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int t = blockIdx.x, ti = 0;
+  const int T = np / 128;
+  while (t >= T - ti) { t -= T - ti; ++ti; }
+  const int tj = ti + t;
+  const int g0 = blockIdx.y * kper, g1 = min(total, g0 + kper);
+  float *P = parts + (size_t)blockIdx.y * np * np;
+  const int row = ti * 128 + warp * 32 + lane;
+
+  if (g0 >= g1) {   // empty coordinate range: the partial tile is zero
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 *dst = reinterpret_cast<float4 *>(P + (size_t)row * np + tj * 128);
+    for (int c = 0; c < 32; ++c) dst[c] = z;
+    return;
+  }
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GT_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     su32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tmem_base;
+
+  const int n_iter = g1 - g0;
+  if (threadIdx.x == 0) {
+    // producer
+    for (int i = 0; i < n_iter; ++i) {
+      const int s = i % GT_STAGES;
+      const uint32_t use = (uint32_t)(i / GT_STAGES);
+      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err)) { abort_flag = 1; break; }
+      if (*(volatile int *)&abort_flag) break;
+      const int g = g0 + i;
+      const int pass = g / KB, kb = g - pass * KB;
+      const CUtensorMap *ma = pass == 2 ? &ml : &mh;
+      const CUtensorMap *mb = pass == 1 ? &ml : &mh;
+      uint8_t *sa = ring + s * GT_STAGE_BYTES;
+      uint8_t *sb = sa + GT_TILE_BYTES;
+      mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
+      tma_load_2d(sa, ma, &full_bar[s], kb * 64, ti * 128);
+      tma_load_2d(sb, mb, &full_bar[s], kb * 64, tj * 128);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    bool ok = true;
+    for (int i = 0; i < n_iter; ++i) {
+      const int s = i % GT_STAGES;
+      const uint32_t use = (uint32_t)(i / GT_STAGES);
+      if (!mbar_wait(&full_bar[s], use & 1u, err)) { ok = false; abort_flag = 1; break; }
+      tc_fence_after();
+      const uint32_t sa = su32(ring + s * GT_STAGE_BYTES);
+      const uint32_t sb = sa + GT_TILE_BYTES;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        umma(tacc, sdesc(sa + k * 32), sdesc(sb + k * 32), (i > 0 || k > 0) ? 1u : 0u);
+      umma_commit(&empty_bar[s]);
+    }
+    (void)ok;
+    umma_commit(&done_bar);
+  }
+  __syncwarp();
+  // epilogue: wait for the accumulator
+  const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err));
+  tc_fence_after();
+  if (done && !*(volatile int *)&abort_flag) {
+    const uint32_t lane_base = tacc + ((uint32_t)(warp * 32) << 16);
+    float *dst = P + (size_t)row * np + tj * 128;
+    for (int c = 0; c < 4; ++c) {
+      uint32_t r[32];
+      tmem_ld32(lane_base + c * 32, r);
+      float4 *d4 = reinterpret_cast<float4 *>(dst + c * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        d4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                            __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+    }
+  }
+  // drain: every stage's copies must have landed before the CTA retires
+  if (threadIdx.x == 0 && abort_flag) {
+    for (int s = 0; s < GT_STAGES && s < n_iter; ++s) {
+      const int last = ((n_iter - 1 - s) / GT_STAGES);
+      mbar_wait(&full_bar[s], (uint32_t)(last & 1), err);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tacc) : "memory");
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+static int make_map(CUtensorMap *m, const __nv_bfloat16 *base, int dp, int np) {
+  auto fn = encode_fn();
+  if (!fn) return VIP_ERR_CUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)np};
+  const cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? VIP_OK : VIP_ERR_CUDA;
+}
+
+int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xl, int n, int dp, int np,
+                   int splits, float *parts, int *err, cudaStream_t st) {
+  if (np % 128 || dp % 64 || ((uintptr_t)Xh & 15) || (Xl && ((uintptr_t)Xl & 15)) || n > np)
+    return VIP_ERR_ARG;
+  CUtensorMap mh, ml;
+  int rc = make_map(&mh, Xh, dp, np);
+  if (rc) return rc;
+  rc = make_map(&ml, Xl ? Xl : Xh, dp, np);
+  if (rc) return rc;
+  const int T = np / 128;
+  const int tiles = T * (T + 1) / 2;
+  const int KB = dp / 64;
+  const int total = KB * (Xl ? 3 : 1);
+  const int kper = (total + splits - 1) / splits;
+  const size_t smem = (size_t)GT_STAGES * GT_STAGE_BYTES + 1024;
+  VIP_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  gram_tc_kernel<<<dim3(tiles, splits), 128, smem, st>>>(mh, ml, KB, kper, total, np, parts, err);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+}  // namespace vip

@@ -1,0 +1,628 @@
+// SVGD (Eq. 13-17) and stochastic SVGD (Eq. 21-25) particle updates.
+//
+// Pipeline of one step on X [n][d], G [n][d] (all kernels below):
+//   1. centre      mean over particles (FP64), Xc = X - mean (FP32) and its
+//                  BF16 hi/lo split for the tensor-core Gram
+//   2. norms       |xc_i|^2 in FP64
+//   3. gram        partial Xc Xc^T over K-splits (tcgen05 BF16 tensor cores,
+//                  or a SIMT FP32 reference path)
+//   4. finish      D2_ij = |xc_i|^2 + |xc_j|^2 - 2 Gram_ij in FP64, clamped at
+//                  0, zero diagonal; upper triangle collected as sort keys
+//   5. median      radix selection of the middle element(s) of all n^2
+//                  entries -> h^2 = med / (2 ln(n+1))
+//   6. kernel      Kbar_ij = exp(-D2_ij / (2 h^2)), row sums r_i
+//   7. (sSVGD)     Lk = chol(Kbar + tau I) (blocked, FP32), noise draws
+//   8. update      one fused GEMM pass over column tiles:
+//                  phi_i = [ (Kbar G)_i + (r_i xc_i - (Kbar Xc)_i) / h^2 ] / n,
+//                  x_i <- clip(x_i + eps phi_i + sqrt(2 eps/n) (Lk Xi)_i, lo, hi)
+// The repulsive term uses the identity sum_j k_ij (m_i - m_j) =
+// r_i xc_i - (Kbar Xc)_i, exact in real arithmetic because the particle
+// mean cancels; centring keeps it well conditioned in FP32.
+#include "common.cuh"
+#include "gram.cuh"
+#include "philox.cuh"
+
+#include <cmath>
+
+namespace vip {
+
+struct SvgdWs {
+  double *mean;
+  float *Xc;
+  __nv_bfloat16 *Xh, *Xl;
+  double *nrm;
+  float *parts;
+  double *D2;
+  unsigned long long *keys;
+  unsigned int *hist;       // [2][256]
+  unsigned long long *sel;  // prefix[2], mask, k[2], zero[2] (as u64)
+  double *h2;
+  int *flag;
+  float *K, *rs;
+  float *Lk, *Xi;
+  int np, dp, splits, M;
+};
+
+static int gram_splits(int n, int d, int gp) {
+  const int np = (n + 127) / 128 * 128;
+  const int t = np / 128;
+  const int tiles = gp == VIP_GRAM_FP32 ? ((n + 63) / 64) * ((n + 63) / 64 + 1) / 2
+                                        : t * (t + 1) / 2;
+  int s = (304 + tiles - 1) / tiles;
+  const int kmax = std::max(1, d / 1024);
+  return std::max(1, std::min(s, kmax));
+}
+
+static size_t layout(int n, int d, int gp, int stochastic, void *base, size_t cap, SvgdWs &w) {
+  Carve cv(base, cap);
+  w.np = (n + 127) / 128 * 128;
+  w.dp = (d + 63) / 64 * 64;
+  w.splits = gram_splits(n, d, gp);
+  w.M = n * (n - 1) / 2;
+  w.mean = cv.take<double>(d);
+  w.Xc = cv.take<float>((size_t)n * d);
+  const bool tc = gp != VIP_GRAM_FP32;
+  w.Xh = cv.take<__nv_bfloat16>(tc ? (size_t)w.np * w.dp : 0);
+  w.Xl = cv.take<__nv_bfloat16>(tc && gp == VIP_GRAM_BF16X3 ? (size_t)w.np * w.dp : 0);
+  w.nrm = cv.take<double>(n);
+  w.parts = cv.take<float>((size_t)w.splits * w.np * w.np);
+  w.D2 = cv.take<double>((size_t)n * n);
+  w.keys = cv.take<unsigned long long>(std::max(w.M, 1));
+  w.hist = cv.take<unsigned int>(512);
+  w.sel = cv.take<unsigned long long>(8);
+  w.h2 = cv.take<double>(2);
+  w.flag = cv.take<int>(4);
+  w.K = cv.take<float>((size_t)n * n);
+  w.rs = cv.take<float>(n);
+  w.Lk = cv.take<float>(stochastic ? (size_t)n * n : 0);
+  w.Xi = cv.take<float>(stochastic ? (size_t)n * d : 0);
+  return cv.off;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void centre_kernel(const float *__restrict__ X, int n, int d, int dp, int np,
+                              double *mean, float *Xc, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= dp) return;
+  if (c >= d) {
+    for (int i = 0; i < np; ++i) {
+      if (Xh) Xh[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
+      if (Xl) Xl[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
+    }
+    return;
+  }
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * d + c];
+  const double m = s / n;
+  mean[c] = m;
+  for (int i = 0; i < n; ++i) {
+    const float xc = (float)((double)X[(size_t)i * d + c] - m);
+    Xc[(size_t)i * d + c] = xc;
+    if (Xh) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(xc);
+      Xh[(size_t)i * dp + c] = h;
+      if (Xl) Xl[(size_t)i * dp + c] = __float2bfloat16_rn(xc - __bfloat162float(h));
+    }
+  }
+  if (Xh)
+    for (int i = n; i < np; ++i) {
+      Xh[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
+      if (Xl) Xl[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+__global__ void norms_kernel(const float *__restrict__ Xc, int d, double *nrm) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    const double v = Xc[(size_t)i * d + c];
+    s += v * v;
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) nrm[i] = t;
+}
+
+// SIMT FP32 Gram partials (reference path): 64x64 upper-triangle tiles.
+__global__ void gram_simt_kernel(const float *__restrict__ Xc, int n, int d, int np, int kchunk,
+                                 float *parts) {
+  __shared__ float As[32][65], Bs[32][65];
+  const int T = (n + 63) / 64;
+  int t = blockIdx.x, ti = 0;
+  while (t >= T - ti) { t -= T - ti; ++ti; }
+  const int tj = ti + t;
+  const int i0 = ti * 64, j0 = tj * 64;
+  const int k0 = blockIdx.y * kchunk, k1 = min(d, k0 + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  for (int kb = k0; kb < k1; kb += 32) {
+    for (int q = threadIdx.x; q < 64 * 32; q += 256) {
+      const int r = q >> 5, kk = q & 31;
+      const int k = kb + kk;
+      As[kk][r] = (i0 + r < n && k < k1) ? Xc[(size_t)(i0 + r) * d + k] : 0.f;
+      Bs[kk][r] = (j0 + r < n && k < k1) ? Xc[(size_t)(j0 + r) * d + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], b[4];
+      for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty * 4 + u]; b[u] = Bs[kk][tx * 4 + u]; }
+      for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  float *P = parts + (size_t)blockIdx.y * np * np;
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < n && j < n) P[(size_t)i * np + j] = acc[u][v];
+    }
+}
+
+__global__ void copy_d2_kernel(const double *D2, size_t nn, double *out) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nn) out[q] = D2[q];
+}
+
+__global__ void d2_finish_kernel(const float *__restrict__ parts, int splits, int n, int np,
+                                 const double *nrm, double *D2, unsigned long long *keys) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= n || j < i) return;
+  double v = 0.0;
+  if (i != j) {
+    double g = 0.0;
+    for (int s = 0; s < splits; ++s) g += (double)parts[(size_t)s * np * np + (size_t)i * np + j];
+    v = nrm[i] + nrm[j] - 2.0 * g;
+    if (!(v > 0.0)) v = 0.0;
+    const long long idx = (long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1);
+    keys[idx] = (unsigned long long)__double_as_longlong(v);
+  }
+  D2[(size_t)i * n + j] = v;
+  D2[(size_t)j * n + i] = v;
+}
+
+// Radix selection of up to two ranks of the multiset {n zeros} U {each upper
+// D2 value twice}. sel: [0..1] prefix, [2] mask, [3..4] rank, [5..6] zero flag.
+__global__ void median_init_kernel(int n, unsigned long long *sel, unsigned int *hist) {
+  const long long N2 = (long long)n * n;
+  long long kf[2];
+  if (N2 % 2 == 0) { kf[0] = N2 / 2 - 1; kf[1] = N2 / 2; }
+  else { kf[0] = kf[1] = (N2 - 1) / 2; }
+  for (int r = 0; r < 2; ++r) {
+    sel[r] = 0ull;
+    const bool z = kf[r] < n;
+    sel[5 + r] = z ? 1ull : 0ull;
+    sel[3 + r] = z ? 0ull : (unsigned long long)((kf[r] - n) / 2);
+  }
+  sel[2] = 0ull;
+  for (int q = 0; q < 512; ++q) hist[q] = 0u;
+}
+
+__global__ void median_hist_kernel(const unsigned long long *__restrict__ keys, int M, int shift,
+                                   const unsigned long long *sel, unsigned int *hist) {
+  __shared__ unsigned int h[512];
+  for (int q = threadIdx.x; q < 512; q += blockDim.x) h[q] = 0u;
+  __syncthreads();
+  const unsigned long long mask = sel[2], p0 = sel[0], p1 = sel[1];
+  const bool z0 = sel[5] != 0ull, z1 = sel[6] != 0ull;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M; e += gridDim.x * blockDim.x) {
+    const unsigned long long u = keys[e];
+    const unsigned dg = (unsigned)((u >> shift) & 255ull);
+    if (!z0 && (u & mask) == p0) atomicAdd(&h[dg], 1u);
+    if (!z1 && (u & mask) == p1) atomicAdd(&h[256 + dg], 1u);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 512; q += blockDim.x)
+    if (h[q]) atomicAdd(&hist[q], h[q]);
+}
+
+__global__ void median_select_kernel(int shift, unsigned long long *sel, unsigned int *hist) {
+  if (threadIdx.x != 0) return;
+  for (int r = 0; r < 2; ++r) {
+    if (sel[5 + r]) continue;
+    unsigned long long k = sel[3 + r], cum = 0ull;
+    for (int dg = 0; dg < 256; ++dg) {
+      const unsigned long long c = hist[r * 256 + dg];
+      if (k < cum + c) {
+        sel[r] |= (unsigned long long)dg << shift;
+        sel[3 + r] = k - cum;
+        break;
+      }
+      cum += c;
+    }
+  }
+  sel[2] |= 255ull << shift;
+  for (int q = 0; q < 512; ++q) hist[q] = 0u;
+}
+
+__global__ void bandwidth_kernel(int n, const unsigned long long *sel, float h2_user,
+                                 const int *gram_err, double *h2, double *h2_out) {
+  double v;
+  if (gram_err && *gram_err) {
+    v = __longlong_as_double(0x7ff8000000000000ll);   // NaN: the Gram did not complete
+  } else if (h2_user > 0.f) {
+    v = h2_user;
+  } else {
+    const double a = sel[5] ? 0.0 : __longlong_as_double((long long)sel[0]);
+    const double b = sel[6] ? 0.0 : __longlong_as_double((long long)sel[1]);
+    const double med = 0.5 * (a + b);
+    v = med < 1e-30 ? 1.0 : med / (2.0 * log((double)n + 1.0));
+  }
+  h2[0] = v;
+  if (h2_out) h2_out[0] = v;
+}
+
+__global__ void kbar_kernel(const double *__restrict__ D2, int n, const double *h2, float *K,
+                            float *rs) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  const double inv = 1.0 / (2.0 * h2[0]);
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const float k = (float)exp(-D2[(size_t)i * n + j] * inv);
+    K[(size_t)i * n + j] = k;
+    s += (double)k;
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) rs[i] = (float)t;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked right-looking Cholesky of A = Kbar + tau I (FP32), lower factor.
+__global__ void chol_init_kernel(const float *K, int n, float tau, float *A, int *flag) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) *flag = 0;
+  if (q >= (size_t)n * n) return;
+  const int i = (int)(q / n), j = (int)(q % n);
+  A[q] = K[q] + (i == j ? tau : 0.f);
+}
+
+constexpr int CB = 32;   // panel width
+
+__global__ void chol_diag_kernel(float *A, int n, int k0, int *flag) {
+  __shared__ float S[CB][CB + 1];
+  const int nb = min(CB, n - k0);
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    S[r][c] = A[(size_t)(k0 + r) * n + k0 + c];
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (threadIdx.x == 0) {
+      float d = S[c][c];
+      if (!(d > 0.f)) { atomicOr(flag, 1); d = 1.f; }
+      S[c][c] = sqrtf(d);
+    }
+    __syncthreads();
+    const float inv = 1.f / S[c][c];
+    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) S[r][c] *= inv;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+      const int r = q / nb, cc = q % nb;
+      if (cc > c && r >= cc) S[r][cc] = fmaf(-S[r][c], S[cc][c], S[r][cc]);
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    A[(size_t)(k0 + r) * n + k0 + c] = c <= r ? S[r][c] : 0.f;
+  }
+}
+
+// Rows below the panel: L21 = A21 L11^{-T}, one row per thread.
+__global__ void chol_trsm_kernel(float *A, int n, int k0) {
+  __shared__ float L[CB][CB + 1];
+  const int nb = min(CB, n - k0);
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    L[r][c] = A[(size_t)(k0 + r) * n + k0 + c];
+  }
+  __syncthreads();
+  const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x[CB];
+  for (int c = 0; c < nb; ++c) {
+    float v = A[(size_t)i * n + k0 + c];
+    for (int t = 0; t < c; ++t) v = fmaf(-x[t], L[c][t], v);
+    x[c] = v / L[c][c];
+    A[(size_t)i * n + k0 + c] = x[c];
+  }
+}
+
+// Trailing update A22 -= L21 L21^T on the lower triangle.
+__global__ void chol_update_kernel(float *A, int n, int k0) {
+  __shared__ float Ai[CB][65], Aj[CB][65];
+  const int nb = min(CB, n - k0);
+  const int k1 = k0 + nb;
+  const int i0 = k1 + blockIdx.y * 64, j0 = k1 + blockIdx.x * 64;
+  if (j0 > i0 + 63) return;
+  for (int q = threadIdx.x; q < 64 * CB; q += 256) {
+    const int r = q / CB, t = q % CB;
+    Ai[t][r] = (i0 + r < n && t < nb) ? A[(size_t)(i0 + r) * n + k0 + t] : 0.f;
+    Aj[t][r] = (j0 + r < n && t < nb) ? A[(size_t)(j0 + r) * n + k0 + t] : 0.f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  for (int t = 0; t < CB; ++t)
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(Ai[t][ty * 4 + u], Aj[t][tx * 4 + v], acc[u][v]);
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < n && j <= i) A[(size_t)i * n + j] -= acc[u][v];
+    }
+}
+
+__global__ void chol_zero_upper_kernel(float *A, int n) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)n * n) return;
+  if ((int)(q % n) > (int)(q / n)) A[q] = 0.f;
+}
+
+__global__ void philox_fill_kernel(float *out, int rows, int cols, uint64_t seed, uint64_t it) {
+  const int nq = (cols + 3) / 4;
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)rows * nq) return;
+  const int i = (int)(q / nq), c4 = (int)(q % nq);
+  const float4 z = philox_normal4(seed, it, (uint32_t)i, (uint32_t)c4);
+  const float zz[4] = {z.x, z.y, z.z, z.w};
+  for (int u = 0; u < 4; ++u) {
+    const int c = c4 * 4 + u;
+    if (c < cols) out[(size_t)i * cols + c] = zz[u];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused update GEMM: per 64x64 tile of (particles x coordinates) accumulate
+// Kbar G, Kbar Xc and (sSVGD) Lk Xi over all particles j, then apply Eq. (17)
+// (and Eq. 22) with the bound reset.
+template <bool NOISE>
+__global__ void __launch_bounds__(256) update_kernel(
+    const float *__restrict__ K, const float *__restrict__ G, const float *__restrict__ Xc,
+    const float *__restrict__ Lk, const float *__restrict__ Xi, const float *__restrict__ rs,
+    const double *h2p, int n, int d, float eps, float gscale, float noise_scale,
+    const float *lo, const float *hi, float *X) {
+  constexpr int BK = 16;
+  __shared__ float Ks[BK][64], Ls[NOISE ? BK : 1][64];
+  __shared__ __align__(16) float Gs[BK][64], Xs[BK][64], Es[NOISE ? BK : 1][64];
+  const int c0 = blockIdx.x * 64, i0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float a1[4][4] = {}, a2[4][4] = {}, a3[4][4] = {};
+  for (int j0 = 0; j0 < n; j0 += BK) {
+    for (int q = threadIdx.x; q < 64 * BK; q += 256) {
+      const int m = q / BK, kk = q % BK;
+      const bool ok = (i0 + m < n) && (j0 + kk < n);
+      Ks[kk][m] = ok ? K[(size_t)(i0 + m) * n + j0 + kk] : 0.f;
+      if (NOISE) Ls[kk][m] = ok ? Lk[(size_t)(i0 + m) * n + j0 + kk] : 0.f;
+    }
+    for (int q = threadIdx.x; q < 64 * BK; q += 256) {
+      const int kk = q / 64, cc = q % 64;
+      const bool ok = (j0 + kk < n) && (c0 + cc < d);
+      const size_t g = (size_t)(j0 + kk) * d + c0 + cc;
+      Gs[kk][cc] = ok ? G[g] : 0.f;
+      Xs[kk][cc] = ok ? Xc[g] : 0.f;
+      if (NOISE) Es[kk][cc] = ok ? Xi[g] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float k4[4], g4[4], x4[4];
+      for (int u = 0; u < 4; ++u) {
+        k4[u] = Ks[kk][ty * 4 + u];
+        g4[u] = Gs[kk][tx * 4 + u];
+        x4[u] = Xs[kk][tx * 4 + u];
+      }
+      for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) {
+          a1[u][v] = fmaf(k4[u], g4[v], a1[u][v]);
+          a2[u][v] = fmaf(k4[u], x4[v], a2[u][v]);
+        }
+      if (NOISE) {
+        float l4[4], e4[4];
+        for (int u = 0; u < 4; ++u) { l4[u] = Ls[kk][ty * 4 + u]; e4[u] = Es[kk][tx * 4 + u]; }
+        for (int u = 0; u < 4; ++u)
+          for (int v = 0; v < 4; ++v) a3[u][v] = fmaf(l4[u], e4[v], a3[u][v]);
+      }
+    }
+    __syncthreads();
+  }
+  const float inv_h2 = (float)(1.0 / h2p[0]);
+  const float inv_n = 1.f / (float)n;
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty * 4 + u;
+    if (i >= n) continue;
+    const float ri = rs[i];
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + tx * 4 + v;
+      if (c >= d) continue;
+      const size_t g = (size_t)i * d + c;
+      const float rep = (fmaf(ri, Xc[g], -a2[u][v])) * inv_h2;
+      const float phi = fmaf(gscale, a1[u][v], rep) * inv_n;
+      float x = fmaf(eps, phi, X[g]);
+      if (NOISE) x = fmaf(noise_scale, a3[u][v], x);
+      if (lo) x = fmaxf(x, lo[c]);
+      if (hi) x = fminf(x, hi[c]);
+      X[g] = x;
+    }
+  }
+}
+
+// Steps 1-5: centring, Gram, FP64 distances and the bandwidth.
+static int distances(const float *X, int n, int d, float h2, int gp, SvgdWs &w,
+                     double *h2_used, cudaStream_t st) {
+  const bool tc = gp != VIP_GRAM_FP32;
+  centre_kernel<<<idiv_up(w.dp, 128), 128, 0, st>>>(X, n, d, w.dp, w.np, w.mean, w.Xc,
+                                                    tc ? w.Xh : nullptr,
+                                                    gp == VIP_GRAM_BF16X3 ? w.Xl : nullptr);
+  VIP_CHECK_LAUNCH();
+  norms_kernel<<<n, 256, 0, st>>>(w.Xc, d, w.nrm);
+  VIP_CHECK_LAUNCH();
+  if (tc) {
+    int rc = gram_tc_launch(w.Xh, gp == VIP_GRAM_BF16X3 ? w.Xl : nullptr, n, w.dp, w.np,
+                            w.splits, w.parts, w.flag + 1, st);
+    if (rc) return rc;
+  } else {
+    const int T = idiv_up(n, 64);
+    const int kchunk = idiv_up(idiv_up(d, w.splits), 32) * 32;
+    gram_simt_kernel<<<dim3(T * (T + 1) / 2, w.splits), 256, 0, st>>>(w.Xc, n, d, w.np, kchunk,
+                                                                       w.parts);
+    VIP_CHECK_LAUNCH();
+  }
+  d2_finish_kernel<<<dim3(idiv_up(n, 128), n), 128, 0, st>>>(w.parts, w.splits, n, w.np, w.nrm,
+                                                             w.D2, w.keys);
+  VIP_CHECK_LAUNCH();
+  if (!(h2 > 0.f)) {
+    median_init_kernel<<<1, 1, 0, st>>>(n, w.sel, w.hist);
+    VIP_CHECK_LAUNCH();
+    if (w.M > 0) {
+      const int blocks = std::min(1024, std::max(1, idiv_up(w.M, 256 * 8)));
+      for (int shift = 56; shift >= 0; shift -= 8) {
+        median_hist_kernel<<<blocks, 256, 0, st>>>(w.keys, w.M, shift, w.sel, w.hist);
+        VIP_CHECK_LAUNCH();
+        median_select_kernel<<<1, 32, 0, st>>>(shift, w.sel, w.hist);
+        VIP_CHECK_LAUNCH();
+      }
+    }
+  }
+  bandwidth_kernel<<<1, 1, 0, st>>>(n, w.sel, h2, tc ? w.flag + 1 : nullptr, w.h2, h2_used);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+static int check_args(const float *X, int n, int d, int gp, void *ws) {
+  if (!X || n < 1 || d < 1 || !ws || ((uintptr_t)ws & 255) ||
+      (gp != VIP_GRAM_BF16 && gp != VIP_GRAM_BF16X3 && gp != VIP_GRAM_FP32))
+    return VIP_ERR_ARG;
+  return VIP_OK;
+}
+
+static int run_svgd(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
+                    const float *lo,
+                    const float *hi, int gp, void *ws, size_t ws_bytes, double *h2_used,
+                    bool stochastic, uint64_t seed, uint64_t it, const float *xi,
+                    double *tau_used, cudaStream_t st) {
+  if (check_args(X, n, d, gp, ws) || !G || !(eps >= 0.f)) return VIP_ERR_ARG;
+  SvgdWs w;
+  const size_t need = layout(n, d, gp, stochastic, ws, ws_bytes, w);
+  if (need > ws_bytes) return VIP_ERR_NOMEM;
+  int rc = distances(X, n, d, h2, gp, w, h2_used, st);
+  if (rc) return rc;
+  kbar_kernel<<<n, 256, 0, st>>>(w.D2, n, w.h2, w.K, w.rs);
+  VIP_CHECK_LAUNCH();
+  const dim3 ug(idiv_up(d, 64), idiv_up(n, 64));
+  if (!stochastic) {
+    update_kernel<false><<<ug, 256, 0, st>>>(w.K, G, w.Xc, nullptr, nullptr, w.rs, w.h2, n, d,
+                                             eps, gscale, 0.f, lo, hi, X);
+    VIP_CHECK_LAUNCH();
+    return VIP_OK;
+  }
+  // sSVGD: jittered Cholesky with retries, then the noisy update
+  double tau = 1e-6 * n;
+  bool ok = false;
+  const size_t nn = (size_t)n * n;
+  for (int attempt = 0; attempt < 4 && !ok; ++attempt, tau *= 10.0) {
+    chol_init_kernel<<<(unsigned)idiv_up((int)std::min(nn, (size_t)1 << 30), 256), 256, 0, st>>>(
+        w.K, n, (float)tau, w.Lk, w.flag);
+    VIP_CHECK_LAUNCH();
+    for (int k0 = 0; k0 < n; k0 += CB) {
+      chol_diag_kernel<<<1, 256, 0, st>>>(w.Lk, n, k0, w.flag);
+      VIP_CHECK_LAUNCH();
+      const int rest = n - k0 - std::min(CB, n - k0);
+      if (rest > 0) {
+        chol_trsm_kernel<<<idiv_up(rest, 128), 128, 0, st>>>(w.Lk, n, k0);
+        VIP_CHECK_LAUNCH();
+        const int nb64 = idiv_up(rest, 64);
+        chol_update_kernel<<<dim3(nb64, nb64), 256, 0, st>>>(w.Lk, n, k0);
+        VIP_CHECK_LAUNCH();
+      }
+    }
+    int hflag = 0;
+    VIP_TRY(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VIP_TRY(cudaStreamSynchronize(st));
+    ok = hflag == 0;
+    if (ok) break;
+  }
+  if (!ok) return VIP_ERR_NOTPD;
+  if (tau_used) VIP_TRY(cudaMemcpyAsync(tau_used, &tau, sizeof(double), cudaMemcpyHostToDevice, st));
+  chol_zero_upper_kernel<<<(unsigned)idiv_up((int)std::min(nn, (size_t)1 << 30), 256), 256, 0, st>>>(
+      w.Lk, n);
+  VIP_CHECK_LAUNCH();
+  const float *noise = xi;
+  if (!noise) {
+    const size_t nq = (size_t)n * idiv_up(d, 4);
+    philox_fill_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(w.Xi, n, d, seed, it);
+    VIP_CHECK_LAUNCH();
+    noise = w.Xi;
+  }
+  const float ns = (float)std::sqrt(2.0 * (double)eps / n);
+  update_kernel<true><<<ug, 256, 0, st>>>(w.K, G, w.Xc, w.Lk, noise, w.rs, w.h2, n, d, eps, gscale,
+                                          ns, lo, hi, X);
+  VIP_CHECK_LAUNCH();
+  // tau is a host local: make the asynchronous copy complete before return
+  if (tau_used) VIP_TRY(cudaStreamSynchronize(st));
+  return VIP_OK;
+}
+
+}  // namespace vip
+
+using namespace vip;
+
+extern "C" {
+
+size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic) {
+  if (n < 1 || d < 1) return 0;
+  SvgdWs w;
+  return layout(n, d, gram_precision, stochastic, nullptr, 0, w) + 256;
+}
+
+int svgd_step(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
+              const float *lo, const float *hi, int gram_precision, void *ws, size_t ws_bytes,
+              double *h2_used, vip_stream_t stream) {
+  return run_svgd(X, G, gscale, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes, h2_used, false, 0,
+                  0, nullptr, nullptr, stream);
+}
+
+int ssvgd_step(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
+               const float *lo, const float *hi, int gram_precision, void *ws, size_t ws_bytes,
+               double *h2_used, uint64_t seed, uint64_t iter, const float *xi,
+               double *tau_used, vip_stream_t stream) {
+  return run_svgd(X, G, gscale, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes, h2_used, true, seed,
+                  iter, xi, tau_used, stream);
+}
+
+int svgd_sqdist(const float *X, int n, int d, int gram_precision, double *D2,
+                double *h2_used, void *ws, size_t ws_bytes, vip_stream_t stream) {
+  if (check_args(X, n, d, gram_precision, ws) || !D2) return VIP_ERR_ARG;
+  SvgdWs w;
+  if (layout(n, d, gram_precision, 0, ws, ws_bytes, w) > ws_bytes) return VIP_ERR_NOMEM;
+  int rc = distances(X, n, d, 0.f, gram_precision, w, h2_used, stream);
+  if (rc) return rc;
+  const size_t nn = (size_t)n * n;
+  copy_d2_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(w.D2, nn, D2);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+int vip_philox_normal(float *out, int rows, int cols, uint64_t seed, uint64_t iter,
+                      vip_stream_t stream) {
+  if (!out || rows < 1 || cols < 1) return VIP_ERR_ARG;
+  const size_t nq = (size_t)rows * idiv_up(cols, 4);
+  philox_fill_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(out, rows, cols, seed, iter);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,5 @@
+// Batched wave kernels with FP16 snapshots and power-of-two block scales.
+#include "wave_inst.cuh"
+namespace vip {
+const void *wave_kernel_f16(int V, int mode) { return wave_kernel_table<__half>(V, mode); }
+}  // namespace vip

@@ -1,0 +1,25 @@
+// Explicit instantiations of the batched wave kernel, one translation unit
+// per snapshot type so that the library compiles in parallel.
+#pragma once
+#include "wave.cuh"
+
+namespace vip {
+
+// Kernel address for (rows per thread V, mode, snapshot type); nullptr when
+// that combination is not built.
+const void *wave_kernel_f32(int V, int mode);
+const void *wave_kernel_bf16(int V, int mode);
+const void *wave_kernel_f16(int V, int mode);
+
+template <class DT>
+const void *wave_kernel_table(int V, int mode) {
+#define VIP_K(VV, MM)                                                  \
+  if (V == VV && mode == MM)                                           \
+    return reinterpret_cast<const void *>(&wave_cluster_kernel<VV, MM, DT>);
+  VIP_K(4, WM_GRADIENT) VIP_K(4, WM_ADJOINT)
+  VIP_K(8, WM_GRADIENT) VIP_K(8, WM_ADJOINT)
+#undef VIP_K
+  return nullptr;
+}
+
+}  // namespace vip

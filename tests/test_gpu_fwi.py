@@ -1,0 +1,197 @@
+"""GPU parity of the FWI path (fwi_forward, fwi_gradient, fwi_adjoint) against
+the FP64 oracle, through the C ABI.
+
+Tolerances: relative L2 <= 1e-5 for FP32 traces and gradients, <= 1e-6 for the
+FP64-reduced misfit (Eq. 26); reduced-precision snapshots are measured and
+held to the bounds stated with each test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle import fwi as ofwi
+import paper_2310_13325_gb300 as vg
+from gpu_common import cfg1_case, cfg1_oracle_gradients, odd_config, problem, rel
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_13325_gb300 import build
+    build.build()
+
+
+def test_forward_traces_match_oracle_cfg1():
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    ref = ofwi.seismograms(V, g)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    out = fwi.forward(_t(V)).cpu().numpy()
+    assert out.shape == ref.shape
+    for p in range(2):
+        for s in range(g.nsrc):
+            assert rel(out[p, s], ref[p, s]) <= 1e-5, (p, s, rel(out[p, s], ref[p, s]))
+    assert fwi.last_status() == 0
+
+
+def test_gradient_and_misfit_match_oracle_cfg1():
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    J_ref, G_ref = cfg1_oracle_gradients(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    J, G = fwi.gradient(_t(V), _t(d_obs), sigma)
+    J = J.cpu().numpy()
+    G = G.reshape(2, -1).cpu().numpy()
+    assert np.all(np.abs(J - J_ref) <= 1e-6 * np.abs(J_ref)), (J, J_ref)
+    for p in range(2):
+        assert rel(G[p], G_ref[p]) <= 1e-5, rel(G[p], G_ref[p])
+
+
+def test_plain_loop_equals_batched_bit_for_bit():
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    Vt, Dt = _t(V), _t(d_obs)
+    Jb, Gb = fwi.gradient(Vt, Dt, sigma)
+    Sb = fwi.forward(Vt)
+    fwi.set_mode(vg.FWI_MODE_PLAIN, 1)
+    Jp, Gp = fwi.gradient(Vt, Dt, sigma)
+    Sp = fwi.forward(Vt)
+    assert torch.equal(Sb, Sp)
+    assert torch.equal(Gb, Gp)
+    assert torch.allclose(Jb, Jp, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("K", [7, 50])
+def test_checkpoint_recompute_equals_store_all(K):
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    Vt, Dt = _t(V), _t(d_obs)
+    J1, G1 = fwi.gradient(Vt, Dt, sigma)
+    G1 = G1.clone()
+    fwi.set_mode(vg.FWI_MODE_BATCHED, K)
+    JK, GK = fwi.gradient(Vt, Dt, sigma)
+    assert torch.equal(G1, GK)
+    assert torch.equal(J1, JK)
+    fwi.set_mode(vg.FWI_MODE_PLAIN, K)
+    Jp, Gp = fwi.gradient(Vt, Dt, sigma)
+    assert torch.equal(G1, Gp)
+
+
+def test_ragged_grid_every_launch_shape_agrees_with_oracle():
+    cfg = odd_config()
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = problem(cfg, 3)
+    J_ref, G_ref = ofwi.gradients(V, g, d_obs, sigma)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    Vt, Dt = _t(V), _t(d_obs)
+    base = None
+    shapes = [(1, 4, 0), (2, 4, 0), (3, 8, 0), (5, 4, 64), (7, 4, 0), (2, 8, 96)]
+    for Q, Vr, T in shapes:
+        fwi.set_plan(Q, Vr, T)
+        J, G = fwi.gradient(Vt, Dt, sigma)
+        G = G.reshape(3, -1).cpu().numpy()
+        for p in range(3):
+            assert rel(G[p], G_ref[p]) <= 1e-5, (Q, Vr, T, p, rel(G[p], G_ref[p]))
+        assert np.all(np.abs(J.cpu().numpy() - J_ref) <= 1e-6 * J_ref)
+        if base is None:
+            base = G
+        else:
+            assert np.array_equal(G, base), (Q, Vr, T)
+
+
+def test_autograd_backward_is_the_oracle_adjoint():
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    rng = np.random.default_rng(12)
+    dseis = rng.standard_normal((2, g.nsrc, g.nrec, g.nt))
+    ref = np.stack([ofwi.adjoint_of_upstream(V[p], g, dseis[p]).reshape(-1)
+                    for p in range(2)])
+    fwi = vg.Fwi.from_config(cfg, geo)
+    v = _t(V).reshape(2, cfg.nz, cfg.nx).requires_grad_(True)
+    seis = vg.FwiSeis.apply(v, fwi)
+    (seis * _t(dseis)).sum().backward()
+    got = v.grad.reshape(2, -1).cpu().numpy()
+    for p in range(2):
+        assert rel(got[p], ref[p]) <= 1e-5, rel(got[p], ref[p])
+
+
+@pytest.mark.parametrize("prec,bound", [(vg.FWI_CKPT_BF16, 2e-2), (vg.FWI_CKPT_FP16, 5e-3)])
+def test_reduced_precision_snapshots_error_is_bounded(prec, bound):
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    J_ref, G_ref = cfg1_oracle_gradients(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    J, G = fwi.gradient(_t(V), _t(d_obs), sigma, precision=prec)
+    G = G.reshape(2, -1).cpu().numpy()
+    errs = [rel(G[p], G_ref[p]) for p in range(2)]
+    print("snapshot precision %d: gradient rel-L2 %s" % (prec, errs))
+    assert max(errs) <= bound
+    # the misfit comes from the FP32 forward sweep and is unaffected
+    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= 1e-6 * J_ref)
+
+
+def test_noise_free_data_give_zero_misfit_and_gradient():
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    vt = _t(v_true)[None]
+    clean = fwi.forward(vt)[0].contiguous()
+    J, G = fwi.gradient(vt, clean, sigma)
+    assert J.item() == 0.0
+    assert torch.count_nonzero(G).item() == 0
+
+
+def test_unstable_velocity_is_reported():
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    v = torch.full((1, cfg.nz, cfg.nx), 6000.0, device=DEV)   # 6000 * 1e-3 / 10 = 0.6
+    fwi.forward(v)
+    assert fwi.last_status() == -2
+    fwi.forward(_t(V))
+    assert fwi.last_status() == 0
+
+
+def test_single_particle_and_source_split_work_items():
+    # P = 1 spreads the sources of one particle over several clusters
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    J_ref, G_ref = cfg1_oracle_gradients(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    plan = fwi.query_plan(1)
+    J, G = fwi.gradient(_t(V[:1]), _t(d_obs), sigma)
+    assert rel(G.reshape(-1).cpu().numpy(), G_ref[0]) <= 1e-5
+    assert abs(J.item() - J_ref[0]) <= 1e-6 * J_ref[0]
+    assert plan["sources_per_item"] >= 1
+
+
+def test_full_size_cfg3_sampled_traces_and_gradient_direction():
+    """cfg3 grid (120 x 300, 2000 steps, 200 receivers) in the launch shape the
+    benchmark uses: traces of sampled (particle, source) pairs against the
+    oracle one by one, and the directional derivative of the misfit."""
+    cfg = synth.config("cfg3")
+    geo = synth.geometry(cfg)
+    g = ofwi.Geom.from_config(cfg, geo)
+    v_true = synth.true_model(cfg)
+    lo, hi = synth.prior_bounds(cfg, v_true)
+    V = synth.particles_from_prior(lo, hi, 2, seed=2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    seis = fwi.forward(_t(V))
+    for p, s in ((0, 0), (1, 13)):
+        ref = ofwi.forward(V[p].reshape(cfg.nz, cfg.nx), g, s)
+        e = rel(seis[p, s].cpu().numpy(), ref)
+        # FP32 leapfrog round-off grows ~ sqrt(steps): 2000 steps
+        assert e <= 3e-5, (p, s, e)
+    # directional derivative at full size (property check, any size)
+    obs = fwi.forward(_t(v_true)[None])[0].contiguous()
+    sigma = 1e-3
+    v0 = _t(V[:1])
+    J0, G0 = fwi.gradient(v0, obs, sigma)
+    dv = torch.randn(v0.shape, generator=torch.Generator(device=DEV).manual_seed(3),
+                     device=DEV) * 2.0
+    h = 0.5
+    Jp, _ = fwi.gradient(v0 + h * dv, obs, sigma)
+    Jm, _ = fwi.gradient(v0 - h * dv, obs, sigma)
+    fd = (Jp.item() - Jm.item()) / (2 * h)
+    an = float((G0.reshape(-1).double() * dv.reshape(-1).double()).sum())
+    assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)
