@@ -121,12 +121,15 @@ int  fwi_set_mode(fwi_ctx *ctx, int mode, int ckpt_every);
  * model picks the launch. fwi_autotune(ctx, P, precision) enables tuning. */
 int  fwi_autotune(fwi_ctx *ctx, int P, int precision);
 
-/* Force the batched launch shape: Q CTAs per cluster (1..16), V rows per
- * thread (4 or 8, 0 = any) and T threads per CTA (multiple of 32, 0 = any);
- * Q = 0 restores automatic choice. A shape that does not fit the device
- * makes later calls return VIP_ERR_UNSUPPORTED. Results do not depend on
- * the shape: every cell update is evaluated identically. */
-int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T);
+/* Force the batched launch shape: Q CTAs per cluster (1..16, 0 = any), V
+ * rows per thread (4 or 8, 0 = any), T threads per CTA (multiple of 32,
+ * 0 = any) and the number of sources one cluster processes per work item
+ * (0 = any). All zeros restore automatic choice. A shape that does not fit
+ * the device makes later calls return VIP_ERR_UNSUPPORTED. Traces and
+ * misfits do not depend on the shape; gradients do not depend on Q, V, T
+ * (every cell update and accumulation is evaluated identically) and are
+ * deterministic for any split of the sources. */
+int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T, int sources_per_item);
 int  fwi_set_autotune(fwi_ctx *ctx, int enable);
 
 /* Describe the plan chosen for P particles: writes up to 8 ints to plan_out
@@ -153,7 +156,7 @@ int  fwi_forward(fwi_ctx *ctx, const float *v, int P, float *seis,
  *          uniform prior's bounds)
  *   precision FWI_FP32 | FWI_CKPT_BF16 | FWI_CKPT_FP16 */
 int  fwi_gradient(fwi_ctx *ctx, const float *v, int P, const float *dobs,
-                  float sigma, double *misfit, float *grad, int precision,
+                  double sigma, double *misfit, float *grad, int precision,
                   vip_stream_t stream);
 
 /* Backward of the seismogram map (the autograd rule of fwi_forward):
@@ -189,7 +192,8 @@ int  fwi_last_status(fwi_ctx *ctx);
  *   h2_used [1] device double, the bandwidth used (may be NULL)
  * ====================================================================== */
 #define VIP_GRAM_BF16    0  /* one BF16 tensor-core Gram, FP32 accumulate  */
-#define VIP_GRAM_BF16X3  1  /* hi/lo BF16 split, three tensor-core products */
+#define VIP_GRAM_BF16X3  1  /* three-piece BF16 split, six tensor-core products:
+                               FP32-class accuracy (dropped terms < 2^-24) */
 #define VIP_GRAM_FP32    2  /* SIMT FP32 Gram without tensor cores (reference) */
 
 size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic);

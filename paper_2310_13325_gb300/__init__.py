@@ -96,10 +96,11 @@ class Fwi:
     def set_mode(self, mode=FWI_MODE_BATCHED, ckpt_every=1):
         check(self._L.fwi_set_mode(self._h, int(mode), int(ckpt_every)), "fwi_set_mode")
 
-    def set_plan(self, Q=0, V=0, T=0):
+    def set_plan(self, Q=0, V=0, T=0, sources_per_item=0):
         """Force the batched launch shape (cluster CTAs, rows per thread,
-        threads per CTA); Q=0 returns to automatic choice."""
-        check(self._L.fwi_set_plan(self._h, int(Q), int(V), int(T)), "fwi_set_plan")
+        threads per CTA, sources per work item); zeros = automatic."""
+        check(self._L.fwi_set_plan(self._h, int(Q), int(V), int(T), int(sources_per_item)),
+              "fwi_set_plan")
 
     def set_autotune(self, enable=True):
         check(self._L.fwi_set_autotune(self._h, int(bool(enable))), "fwi_set_autotune")
@@ -119,11 +120,16 @@ class Fwi:
         return self._L.fwi_last_status(self._h)
 
     def _models(self, v):
-        torch = _torch()
-        if v.dim() == 2:
-            v = v.unsqueeze(0)
-        if tuple(v.shape[1:]) != (self.nz, self.nx) and v.shape[-1] != self.nz * self.nx:
-            raise ValueError("models must be [P, nz, nx] or [P, nz*nx]")
+        """Accept one model [nz, nx] or a batch [P, nz, nx] / [P, nz*nx]."""
+        d = self.nz * self.nx
+        if tuple(v.shape) == (self.nz, self.nx) or (v.dim() == 1 and v.numel() == d):
+            v = v.reshape(1, d)
+        elif v.dim() == 3 and tuple(v.shape[1:]) == (self.nz, self.nx):
+            pass
+        elif v.dim() == 2 and v.shape[1] == d:
+            pass
+        else:
+            raise ValueError("models must be [nz, nx], [P, nz, nx] or [P, nz*nx]")
         return v.reshape(v.shape[0], self.nz, self.nx).contiguous(), v.shape[0]
 
     def forward(self, v, out=None, stream=None):

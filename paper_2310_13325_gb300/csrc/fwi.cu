@@ -77,7 +77,7 @@ struct fwi_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   std::map<std::tuple<int, int, int>, std::array<int, 3>> tuned;   // (P,mode,dtype) -> Q,V,T
-  int force_Q = 0, force_V = 0, force_T = 0;                         // launch override
+  int force_Q = 0, force_V = 0, force_T = 0, force_spi = 0;          // launch override
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
   int *pl_recmap = nullptr;
@@ -189,7 +189,10 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
   auto a = [](size_t n, size_t es) { return align_up(n * es, 256); };
   pl.slot_bytes = a(pl.Dslot, dtype_size(pl.dtype)) + a(pl.DSslot, 4) + a(pl.rhoslot, 4) +
                   a(pl.GPslot, 4) + a(pl.CKslot, 4) + a(pl.ASslot, 4);
-  pl.total_bytes = align_up((size_t)P * c->S * pl.Q * 8, 256) + (size_t)pl.ncl * pl.slot_bytes;
+  const size_t gi = (pl.mode != WM_FORWARD && pl.ipp > 1)
+                        ? align_up((size_t)P * pl.ipp * c->nz * c->nx * 4, 256) : 0;
+  pl.total_bytes = align_up((size_t)P * c->S * pl.Q * 8, 256) + gi +
+                   (size_t)pl.ncl * pl.slot_bytes;
 }
 
 static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<Plan> &out) {
@@ -244,6 +247,7 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
         double best = 1e300;
         for (int ipp = 1; ipp <= c->S; ++ipp) {
           const int spi = idiv_up(c->S, ipp);
+          if (c->force_spi && spi != std::min(c->force_spi, c->S)) continue;
           const int ipp2 = idiv_up(c->S, spi);
           const int items = P * ipp2;
           const int waves = idiv_up(items, std::min(items, ncl));
@@ -288,9 +292,9 @@ static int choose_plan(fwi_ctx *c, int P, int mode, int dtype, Plan &out) {
   auto key = std::make_tuple(P, mode, dtype);
   auto it = c->tuned.find(key);
   const Plan *pick = nullptr;
-  if (c->force_Q) {
+  if (c->force_Q || c->force_spi) {
     for (auto &p : cand)
-      if (p.Q == c->force_Q && (!c->force_V || p.V == c->force_V) &&
+      if ((!c->force_Q || p.Q == c->force_Q) && (!c->force_V || p.V == c->force_V) &&
           (!c->force_T || p.T == c->force_T) && (!pick || p.est < pick->est))
         pick = &p;
     if (!pick) return VIP_ERR_UNSUPPORTED;
@@ -328,6 +332,16 @@ static int ensure_scratch(fwi_ctx *c, size_t bytes) {
   return VIP_OK;
 }
 
+// Ordered sum of the partial gradients of the work items of each particle.
+__global__ void grad_merge_kernel(const float *GI, int P, int ipp, int d, float *grad) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)P * d) return;
+  const size_t p = q / d, i = q - p * d;
+  float acc = 0.f;
+  for (int k = 0; k < ipp; ++k) acc += GI[(p * ipp + k) * d + i];
+  grad[q] = acc;
+}
+
 __global__ void j_reduce_kernel(const double *Jpart, int P, int S, int Q, double scale,
                                 double *misfit) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -344,7 +358,6 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   wp.N = c->N; wp.S = c->S; wp.R = c->R;
   wp.dtdx = (float)((double)c->dt / (double)c->dx);
   wp.dx2 = c->dx * c->dx;
-  wp.c0x2 = (float)(2.0 * kC8[0]);
   wp.c1 = (float)kC8[1]; wp.c2 = (float)kC8[2]; wp.c3 = (float)kC8[3]; wp.c4 = (float)kC8[4];
   wp.w_cfl = (float)cfl_w_limit();
   wp.Q = pl.Q; wp.Hb = pl.Hb; wp.NXg = pl.NXg; wp.PX = pl.PX;
@@ -359,6 +372,8 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   // scratch carve
   Carve cv(c->scratch, c->scratch_bytes);
   wp.Jpart = cv.take<double>((size_t)P * c->S * pl.Q);
+  wp.GI = cv.take<float>((pl.mode != WM_FORWARD && pl.ipp > 1)
+                             ? (size_t)P * pl.ipp * c->nz * c->nx : 0);
   char *slots = cv.take<char>((size_t)pl.ncl * pl.slot_bytes);
   size_t off = 0;
   auto sub = [&](size_t n, size_t es) {
@@ -409,15 +424,19 @@ static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream
 
 // Enqueue one batched call (no graph): status reset, optional grad zeroing,
 // the persistent kernel, the misfit reduction.
-static int enqueue_batched(fwi_ctx *c, const Plan &pl, WaveParams &wp, int P, float sigma,
+static int enqueue_batched(fwi_ctx *c, const Plan &pl, WaveParams &wp, int P, double sigma,
                            double *misfit, cudaStream_t st) {
   VIP_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
-  if (pl.mode != WM_FORWARD && wp.grad_atomic)
-    VIP_TRY(cudaMemsetAsync(wp.grad, 0, (size_t)P * c->nz * c->nx * 4, st));
   int rc = launch_wave(pl, wp, pl.ncl, st);
   if (rc) return rc;
+  if (pl.mode != WM_FORWARD && wp.grad_atomic) {
+    const size_t tot = (size_t)P * c->nz * c->nx;
+    grad_merge_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(wp.GI, P, pl.ipp,
+                                                                     c->nz * c->nx, wp.grad);
+    VIP_CHECK_LAUNCH();
+  }
   if (pl.mode == WM_GRADIENT && misfit) {
-    const double scale = 0.5 / ((double)sigma * (double)sigma);
+    const double scale = 0.5 / (sigma * sigma);
     j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(wp.Jpart, P, c->S, pl.Q, scale, misfit);
     VIP_CHECK_LAUNCH();
   }
@@ -425,10 +444,10 @@ static int enqueue_batched(fwi_ctx *c, const Plan &pl, WaveParams &wp, int P, fl
 }
 
 static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
-                         const float *dobs, const float *dseis, float sigma, cudaStream_t st);
+                         const float *dobs, const float *dseis, double sigma, cudaStream_t st);
 
 static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float *dobs,
-                       const float *dseis, float sigma, double *misfit, float *grad,
+                       const float *dseis, double sigma, double *misfit, float *grad,
                        float *seis, int dtype, cudaStream_t st) {
   if (c->autotune && !c->tuned.count(std::make_tuple(P, mode, dtype))) {
     int rc = autotune_plan(c, P, mode, dtype, v, dobs, dseis, sigma, st);
@@ -446,11 +465,10 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
   rc = fill_params(c, pl, tb, P, wp);
   if (rc) return rc;
   wp.P = P; wp.v = v; wp.dobs = dobs; wp.dseis = dseis; wp.seis = seis; wp.grad = grad;
-  wp.rho_scale = mode == WM_GRADIENT ? (float)((double)wp.dx2 / ((double)sigma * sigma))
-                                     : wp.dx2;
+  wp.rho_scale = mode == WM_GRADIENT ? (float)((double)wp.dx2 / (sigma * sigma)) : wp.dx2;
   // graph replay keyed by everything the launch depends on
-  uint32_t sigma_bits;
-  memcpy(&sigma_bits, &sigma, 4);
+  uint64_t sigma_bits;
+  memcpy(&sigma_bits, &sigma, 8);
   std::array<uintptr_t, 12> key = {
       (uintptr_t)mode, (uintptr_t)P, (uintptr_t)dtype, (uintptr_t)v, (uintptr_t)dobs,
       (uintptr_t)dseis, (uintptr_t)seis, (uintptr_t)misfit, (uintptr_t)grad,
@@ -489,7 +507,7 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
 // Autotuning: time the candidate launches on a one-wave, short-run problem
 // built from the caller's own inputs, keep the fastest.
 static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
-                         const float *dobs, const float *dseis, float sigma, cudaStream_t st) {
+                         const float *dobs, const float *dseis, double sigma, cudaStream_t st) {
   std::vector<Plan> cand;
   int rc = make_candidates(c, P, mode, dtype, cand);
   if (rc) return rc;
@@ -522,7 +540,7 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
     WaveParams wp;
     if ((rc = fill_params(c, pl, tb, P, wp))) break;
     wp.P = P; wp.v = v; wp.dobs = dobs; wp.dseis = dseis;
-    wp.seis = tmp_out; wp.grad = tmp_out; wp.grad_atomic = 1;
+    wp.seis = tmp_out; wp.grad = tmp_out; wp.grad_atomic = 0;
     wp.rho_scale = 1.f;
     wp.items = pl.items;
     if ((rc = prepare_wave(pl))) break;
@@ -604,7 +622,7 @@ static int ensure_plain(fwi_ctx *c) {
 }
 
 static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *dobs,
-                     const float *dseis, float sigma, double *misfit, float *grad, float *seis,
+                     const float *dseis, double sigma, double *misfit, float *grad, float *seis,
                      cudaStream_t st) {
   int rc = ensure_plain(c);
   if (rc) return rc;
@@ -628,12 +646,12 @@ static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *d
   float *rho = cv.take<float>(rhon);
   PlainParams q;
   q.NZ = c->NZ; q.NX = c->NX; q.N = N; q.R = c->R;
-  q.c0x2 = (float)(2.0 * kC8[0]); q.c1 = (float)kC8[1]; q.c2 = (float)kC8[2];
+  q.c1 = (float)kC8[1]; q.c2 = (float)kC8[2];
   q.c3 = (float)kC8[3]; q.c4 = (float)kC8[4];
   q.gz = c->pl_gz; q.gx = c->pl_gx; q.W = c->pl_W; q.recmap = c->pl_recmap;
   const float dtdx = (float)((double)c->dt / (double)c->dx);
   const float dx2 = c->dx * c->dx;
-  const float rho_scale = (float)((double)dx2 / ((double)sigma * sigma));
+  const float rho_scale = (float)((double)dx2 / (sigma * sigma));
   std::vector<float> wav(N);
   for (int n = 0; n < N; ++n) {
     const double tau = n * (double)c->dt - c->t0;
@@ -716,7 +734,7 @@ static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *d
   }
   if (mode == WM_GRADIENT && misfit) {
     j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(c->pl_J, P, c->S, 1,
-                                                     0.5 / ((double)sigma * sigma), misfit);
+                                                     0.5 / (sigma * sigma), misfit);
     VIP_CHECK_LAUNCH();
   }
   c->last_stream = st;
@@ -837,10 +855,11 @@ int fwi_set_mode(fwi_ctx *c, int mode, int ckpt_every) {
   return VIP_OK;
 }
 
-int fwi_set_plan(fwi_ctx *c, int Q, int V, int T) {
-  if (!c || Q < 0 || Q > 16 || (V != 0 && V != 4 && V != 8) || T < 0 || T > 512 || (T % 32))
+int fwi_set_plan(fwi_ctx *c, int Q, int V, int T, int sources_per_item) {
+  if (!c || Q < 0 || Q > 16 || (V != 0 && V != 4 && V != 8) || T < 0 || T > 512 || (T % 32) ||
+      sources_per_item < 0)
     return VIP_ERR_ARG;
-  c->force_Q = Q; c->force_V = V; c->force_T = T;
+  c->force_Q = Q; c->force_V = V; c->force_T = T; c->force_spi = sources_per_item;
   return VIP_OK;
 }
 
@@ -877,7 +896,7 @@ int fwi_forward(fwi_ctx *c, const float *v, int P, float *seis, vip_stream_t str
                      FWI_FP32, stream);
 }
 
-int fwi_gradient(fwi_ctx *c, const float *v, int P, const float *dobs, float sigma,
+int fwi_gradient(fwi_ctx *c, const float *v, int P, const float *dobs, double sigma,
                  double *misfit, float *grad, int precision, vip_stream_t stream) {
   int rc = check_call(c, v, P);
   if (rc) return rc;

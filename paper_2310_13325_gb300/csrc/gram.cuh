@@ -9,10 +9,12 @@ namespace vip {
 // Partial Gram sums of the upper-triangle 128x128 tiles, split along the
 // coordinate axis: parts[split][i][j] (np x np per split, np a multiple of
 // 128). Xh [np][dp] is the BF16 image of the centred particles (rows >= n and
-// columns >= d zero), Xl the BF16 residual x - bf16(x) or NULL; with Xl the
-// product is hi.hi + hi.lo + lo.hi (three passes). dp is a multiple of 64.
+// columns >= d zero). With Xm, Xl (the BF16 pieces of the successive
+// remainders, x ~ h + m + l) the product is accumulated from the six terms
+// hh + hm + mh + hl + lh + mm, whose dropped terms are below 2^-24 |x||y|;
+// with Xm = Xl = NULL it is the single product hh. dp is a multiple of 64.
 // err: device word, bit 0 set when a bounded wait inside the kernel expired.
-int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xl, int n, int dp, int np,
-                   int splits, float *parts, int *err, cudaStream_t st);
+int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_bfloat16 *Xl,
+                   int n, int dp, int np, int splits, float *parts, int *err, cudaStream_t st);
 
 }  // namespace vip

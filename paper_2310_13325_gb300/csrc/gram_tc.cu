@@ -133,7 +133,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Pass p of the split product uses pieces (A, B) = (kPassA[p], kPassB[p])
+// with 0 = h, 1 = m, 2 = l: hh, hm, mh, hl, lh, mm.
+__constant__ int kPassA[6] = {0, 0, 1, 0, 2, 1};
+__constant__ int kPassB[6] = {0, 1, 0, 2, 0, 1};
+
 __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap mh,
+                                                         const __grid_constant__ CUtensorMap mm,
                                                          const __grid_constant__ CUtensorMap ml,
                                                          int KB, int kper, int total, int np,
                                                          float *parts, int *err) {
@@ -192,8 +198,9 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
       if (*(volatile int *)&abort_flag) break;
       const int g = g0 + i;
       const int pass = g / KB, kb = g - pass * KB;
-      const CUtensorMap *ma = pass == 2 ? &ml : &mh;
-      const CUtensorMap *mb = pass == 1 ? &ml : &mh;
+      const int pa = kPassA[pass], pb = kPassB[pass];
+      const CUtensorMap *ma = pa == 0 ? &mh : (pa == 1 ? &mm : &ml);
+      const CUtensorMap *mb = pb == 0 ? &mh : (pb == 1 ? &mm : &ml);
       uint8_t *sa = ring + s * GT_STAGE_BYTES;
       uint8_t *sb = sa + GT_TILE_BYTES;
       mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
@@ -276,25 +283,29 @@ static int make_map(CUtensorMap *m, const __nv_bfloat16 *base, int dp, int np) {
   return r == CUDA_SUCCESS ? VIP_OK : VIP_ERR_CUDA;
 }
 
-int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xl, int n, int dp, int np,
-                   int splits, float *parts, int *err, cudaStream_t st) {
-  if (np % 128 || dp % 64 || ((uintptr_t)Xh & 15) || (Xl && ((uintptr_t)Xl & 15)) || n > np)
+int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_bfloat16 *Xl,
+                   int n, int dp, int np, int splits, float *parts, int *err, cudaStream_t st) {
+  if (np % 128 || dp % 64 || ((uintptr_t)Xh & 15) || (!Xm) != (!Xl) ||
+      (Xm && (((uintptr_t)Xm & 15) || ((uintptr_t)Xl & 15))) || n > np)
     return VIP_ERR_ARG;
-  CUtensorMap mh, ml;
+  CUtensorMap mh, mm, ml;
   int rc = make_map(&mh, Xh, dp, np);
+  if (rc) return rc;
+  rc = make_map(&mm, Xm ? Xm : Xh, dp, np);
   if (rc) return rc;
   rc = make_map(&ml, Xl ? Xl : Xh, dp, np);
   if (rc) return rc;
   const int T = np / 128;
   const int tiles = T * (T + 1) / 2;
   const int KB = dp / 64;
-  const int total = KB * (Xl ? 3 : 1);
+  const int total = KB * (Xm ? 6 : 1);
   const int kper = (total + splits - 1) / splits;
   const size_t smem = (size_t)GT_STAGES * GT_STAGE_BYTES + 1024;
   VIP_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-  gram_tc_kernel<<<dim3(tiles, splits), 128, smem, st>>>(mh, ml, KB, kper, total, np, parts, err);
+  gram_tc_kernel<<<dim3(tiles, splits), 128, smem, st>>>(mh, mm, ml, KB, kper, total, np, parts,
+                                                         err);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }

@@ -8,7 +8,7 @@ namespace vip {
 // Plain per-step kernels: one cell per thread, fields in global memory.
 struct PlainParams {
   int NZ, NX, N, R;
-  float c0x2, c1, c2, c3, c4;
+  float c1, c2, c3, c4;
   const float *gz, *gx;     // [NZ], [NX]
   const float *W;           // [NZ][NX] w'
   const int *recmap;        // [NZ][NX] receiver number or -1
@@ -36,7 +36,7 @@ __global__ void plain_fwd_step(PlainParams q, const float *__restrict__ cur, flo
   }
   const float u = cur[idx];
   WaveParams wp;
-  wp.c0x2 = q.c0x2; wp.c1 = q.c1; wp.c2 = q.c2; wp.c3 = q.c3; wp.c4 = q.c4;
+  wp.c1 = q.c1; wp.c2 = q.c2; wp.c3 = q.c3; wp.c4 = q.c4;
   float s = lap_cell(wp, u, h, vv);
   if (z == sz && x == sx) s = __fadd_rn(s, fval);
   if (D) D[idx] = s;
@@ -46,9 +46,9 @@ __global__ void plain_fwd_step(PlainParams q, const float *__restrict__ cur, flo
   if (r >= 0) {
     if (seis) seis[(size_t)r * q.N + n] = an;
     if (rho) {
-      const float res = __fsub_rn(an, dobs_s[(size_t)r * q.N + n]);
-      rho[(size_t)r * q.N + n] = __fmul_rn(res, rho_scale);
-      atomicAdd(J, (double)res * (double)res);
+      const double res = (double)an - (double)dobs_s[(size_t)r * q.N + n];
+      rho[(size_t)r * q.N + n] = (float)(res * (double)rho_scale);
+      atomicAdd(J, res * res);
     }
   }
 }
@@ -70,7 +70,7 @@ __global__ void plain_adj_step(PlainParams q, const float *__restrict__ cur, flo
   }
   const float u = cur[idx];
   WaveParams wp;
-  wp.c0x2 = q.c0x2; wp.c1 = q.c1; wp.c2 = q.c2; wp.c3 = q.c3; wp.c4 = q.c4;
+  wp.c1 = q.c1; wp.c2 = q.c2; wp.c3 = q.c3; wp.c4 = q.c4;
   float s = lap_cell(wp, u, h, vv);
   const int r = q.recmap[idx];
   if (r >= 0) {

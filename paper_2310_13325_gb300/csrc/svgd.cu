@@ -2,7 +2,8 @@
 //
 // Pipeline of one step on X [n][d], G [n][d] (all kernels below):
 //   1. centre      mean over particles (FP64), Xc = X - mean (FP32) and its
-//                  BF16 hi/lo split for the tensor-core Gram
+//                  BF16 image (one piece, or the three-piece split
+//                  xc ~ h + m + l for FP32-class accuracy)
 //   2. norms       |xc_i|^2 in FP64
 //   3. gram        partial Xc Xc^T over K-splits (tcgen05 BF16 tensor cores,
 //                  or a SIMT FP32 reference path)
@@ -29,7 +30,7 @@ namespace vip {
 struct SvgdWs {
   double *mean;
   float *Xc;
-  __nv_bfloat16 *Xh, *Xl;
+  __nv_bfloat16 *Xh, *Xm, *Xl;   // BF16 pieces: x ~ h + m + l
   double *nrm;
   float *parts;
   double *D2;
@@ -63,6 +64,7 @@ static size_t layout(int n, int d, int gp, int stochastic, void *base, size_t ca
   w.Xc = cv.take<float>((size_t)n * d);
   const bool tc = gp != VIP_GRAM_FP32;
   w.Xh = cv.take<__nv_bfloat16>(tc ? (size_t)w.np * w.dp : 0);
+  w.Xm = cv.take<__nv_bfloat16>(tc && gp == VIP_GRAM_BF16X3 ? (size_t)w.np * w.dp : 0);
   w.Xl = cv.take<__nv_bfloat16>(tc && gp == VIP_GRAM_BF16X3 ? (size_t)w.np * w.dp : 0);
   w.nrm = cv.take<double>(n);
   w.parts = cv.take<float>((size_t)w.splits * w.np * w.np);
@@ -81,13 +83,15 @@ static size_t layout(int n, int d, int gp, int stochastic, void *base, size_t ca
 
 // ---------------------------------------------------------------------------
 __global__ void centre_kernel(const float *__restrict__ X, int n, int d, int dp, int np,
-                              double *mean, float *Xc, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl) {
+                              double *mean, float *Xc, __nv_bfloat16 *Xh, __nv_bfloat16 *Xm,
+                              __nv_bfloat16 *Xl) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= dp) return;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
   if (c >= d) {
     for (int i = 0; i < np; ++i) {
-      if (Xh) Xh[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
-      if (Xl) Xl[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
+      if (Xh) Xh[(size_t)i * dp + c] = z;
+      if (Xm) { Xm[(size_t)i * dp + c] = z; Xl[(size_t)i * dp + c] = z; }
     }
     return;
   }
@@ -99,15 +103,21 @@ __global__ void centre_kernel(const float *__restrict__ X, int n, int d, int dp,
     const float xc = (float)((double)X[(size_t)i * d + c] - m);
     Xc[(size_t)i * d + c] = xc;
     if (Xh) {
+      // three-piece BF16 split: each remainder is exact in FP32
       const __nv_bfloat16 h = __float2bfloat16_rn(xc);
       Xh[(size_t)i * dp + c] = h;
-      if (Xl) Xl[(size_t)i * dp + c] = __float2bfloat16_rn(xc - __bfloat162float(h));
+      if (Xm) {
+        const float r1 = xc - __bfloat162float(h);
+        const __nv_bfloat16 mm = __float2bfloat16_rn(r1);
+        Xm[(size_t)i * dp + c] = mm;
+        Xl[(size_t)i * dp + c] = __float2bfloat16_rn(r1 - __bfloat162float(mm));
+      }
     }
   }
   if (Xh)
     for (int i = n; i < np; ++i) {
-      Xh[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
-      if (Xl) Xl[(size_t)i * dp + c] = __float2bfloat16_rn(0.f);
+      Xh[(size_t)i * dp + c] = z;
+      if (Xm) { Xm[(size_t)i * dp + c] = z; Xl[(size_t)i * dp + c] = z; }
     }
 }
 
@@ -464,14 +474,15 @@ __global__ void __launch_bounds__(256) update_kernel(
 static int distances(const float *X, int n, int d, float h2, int gp, SvgdWs &w,
                      double *h2_used, cudaStream_t st) {
   const bool tc = gp != VIP_GRAM_FP32;
+  const bool x3 = gp == VIP_GRAM_BF16X3;
   centre_kernel<<<idiv_up(w.dp, 128), 128, 0, st>>>(X, n, d, w.dp, w.np, w.mean, w.Xc,
-                                                    tc ? w.Xh : nullptr,
-                                                    gp == VIP_GRAM_BF16X3 ? w.Xl : nullptr);
+                                                    tc ? w.Xh : nullptr, x3 ? w.Xm : nullptr,
+                                                    x3 ? w.Xl : nullptr);
   VIP_CHECK_LAUNCH();
   norms_kernel<<<n, 256, 0, st>>>(w.Xc, d, w.nrm);
   VIP_CHECK_LAUNCH();
   if (tc) {
-    int rc = gram_tc_launch(w.Xh, gp == VIP_GRAM_BF16X3 ? w.Xl : nullptr, n, w.dp, w.np,
+    int rc = gram_tc_launch(w.Xh, x3 ? w.Xm : nullptr, x3 ? w.Xl : nullptr, n, w.dp, w.np,
                             w.splits, w.parts, w.flag + 1, st);
     if (rc) return rc;
   } else {

@@ -54,7 +54,7 @@ struct WaveParams {
   int nz, nx, nb, NZ, NX, N, S, R;
   float dtdx;            // dt / dx
   float dx2;             // dx^2
-  float c0x2, c1, c2, c3, c4;   // 2 c0 and c1..c4 of the 8th-order stencil
+  float c1, c2, c3, c4;   // c1..c4 of the 8th-order stencil (c0 = -2 sum c_k)
   float w_cfl;           // largest stable w' = (v dt/dx)^2
   // band decomposition
   int Q, Hb, NXg, PX, ntask, ntask_pad, nwblk;
@@ -77,7 +77,9 @@ struct WaveParams {
   float *seis;           // [P][S][R][N]
   double *Jpart;         // [P*S][Q] sum of squared residuals per CTA
   float *grad;           // [P][nz][nx]
-  int grad_atomic;       // 1 when several work items share a particle
+  int grad_atomic;       // 1 when several work items share a particle: each
+                         // item then writes its partial gradient to GI
+  float *GI;             // [items][nz][nx] partial gradients (split items)
   int *status;           // bit 0: CFL violation
   // per-cluster scratch slots
   void *Dbuf;   size_t Dslot;    // snapshot elements per slot
@@ -147,18 +149,25 @@ __device__ __forceinline__ float comp(const float4 &v, int j) {
   return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
-// Laplacian bracket of one cell: 2 c0 u + sum_k c_k ((h-k + h+k) + (v-k + v+k)),
-// every operation rounded explicitly so that all kernels agree bit for bit.
+// Laplacian bracket of one cell, 2 c0 u + sum_k c_k (h_k + v_k) with h_k, v_k
+// the sums of the two neighbours at distance k along x and z. Because the
+// coefficients sum to zero (c0 = -2 sum_k c_k) it equals
+//   sum_k c_k [ ((h_k + v_k) - 4u) ],
+// which is evaluated here, smallest coefficients first: the bracketed
+// differences are small and nearly exact, so the FP32 rounding error of the
+// bracket stays proportional to the bracket itself instead of to the 5.7 u
+// that the first form cancels. Every operation is rounded explicitly so that
+// all kernels agree bit for bit.
+// h[0..7] = u at offsets -4,-3,-2,-1,+1,+2,+3,+4 along x; vv likewise along z.
 __device__ __forceinline__ float lap_cell(const WaveParams &p, float u,
                                           const float h[8], const float vv[8]) {
-  float s = __fmul_rn(p.c0x2, u);
-  s = __fmaf_rn(p.c1, __fadd_rn(__fadd_rn(h[3], h[4]), __fadd_rn(vv[3], vv[4])), s);
-  s = __fmaf_rn(p.c2, __fadd_rn(__fadd_rn(h[2], h[5]), __fadd_rn(vv[2], vv[5])), s);
-  s = __fmaf_rn(p.c3, __fadd_rn(__fadd_rn(h[1], h[6]), __fadd_rn(vv[1], vv[6])), s);
-  s = __fmaf_rn(p.c4, __fadd_rn(__fadd_rn(h[0], h[7]), __fadd_rn(vv[0], vv[7])), s);
+  const float u4 = __fmul_rn(4.f, u);
+  float s = __fmul_rn(p.c4, __fsub_rn(__fadd_rn(__fadd_rn(h[0], h[7]), __fadd_rn(vv[0], vv[7])), u4));
+  s = __fmaf_rn(p.c3, __fsub_rn(__fadd_rn(__fadd_rn(h[1], h[6]), __fadd_rn(vv[1], vv[6])), u4), s);
+  s = __fmaf_rn(p.c2, __fsub_rn(__fadd_rn(__fadd_rn(h[2], h[5]), __fadd_rn(vv[2], vv[5])), u4), s);
+  s = __fmaf_rn(p.c1, __fsub_rn(__fadd_rn(__fadd_rn(h[3], h[4]), __fadd_rn(vv[3], vv[4])), u4), s);
   return s;
 }
-// h[0..7] = u at offsets -4,-3,-2,-1,+1,+2,+3,+4 along one axis.
 
 // New value of a cell from the bracket s, own value u, previous value ap.
 __device__ __forceinline__ float update_cell(float g, float w, float s, float u,
@@ -323,9 +332,11 @@ __device__ __forceinline__ void band_step(const WaveParams &p, const Band &B,
             if (MODE == WM_FORWARD) {
               p.seis[((size_t)a.pair * p.R + rr) * p.N + a.t] = d;
             } else if (MODE == WM_GRADIENT) {
-              const float res = __fsub_rn(d, p.dobs[((size_t)a.s * p.R + rr) * p.N + a.t]);
-              *a.Jacc += (double)res * (double)res;
-              p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + a.t] = __fmul_rn(res, p.rho_scale);
+              const double res =
+                  (double)d - (double)p.dobs[((size_t)a.s * p.R + rr) * p.N + a.t];
+              *a.Jacc = __fma_rn(res, res, *a.Jacc);
+              p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + a.t] =
+                  (float)(res * (double)p.rho_scale);
             }
           }
         }
@@ -539,9 +550,8 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
         for (int x = xa; x <= xb; ++x) acc += (double)GP[(size_t)z * p.NX + x];
       const float vv = vp[(size_t)iz * p.nx + ix];
       const float val = (float)(acc * 2.0 / ((double)vv * (double)p.dx2));
-      float *gp = p.grad + ((size_t)pp * p.nz + iz) * p.nx + ix;
-      if (p.grad_atomic) atomicAdd(gp, val);
-      else *gp = val;
+      if (p.grad_atomic) p.GI[((size_t)item * p.nz + iz) * p.nx + ix] = val;
+      else p.grad[((size_t)pp * p.nz + iz) * p.nx + ix] = val;
     }
     cluster.sync();
   }

@@ -1,9 +1,13 @@
 """GPU parity of the FWI path (fwi_forward, fwi_gradient, fwi_adjoint) against
 the FP64 oracle, through the C ABI.
 
-Tolerances: relative L2 <= 1e-5 for FP32 traces and gradients, <= 1e-6 for the
-FP64-reduced misfit (Eq. 26); reduced-precision snapshots are measured and
-held to the bounds stated with each test.
+Tolerances: relative L2 <= 1e-5 for FP32 traces and gradients driven by data
+residuals. The misfit (Eq. 26) is reduced in FP64: its reduction is held to
+1e-10 against an FP64 sum of the same GPU traces, and its value against the
+oracle to J_TOL, derived from the trace tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <=
+2 (|d| / |r|) rel(d) with |d| / |r| <= 1.5 for prior particles, so 3e-5.
+Reduced-precision snapshots are measured and held to the bounds stated with
+each test.
 """
 import numpy as np
 import pytest
@@ -17,6 +21,7 @@ from gpu_common import cfg1_case, cfg1_oracle_gradients, odd_config, problem, re
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
+J_TOL = 3e-5
 
 
 def _t(a, dtype=torch.float32):
@@ -48,15 +53,22 @@ def test_gradient_and_misfit_match_oracle_cfg1():
     J, G = fwi.gradient(_t(V), _t(d_obs), sigma)
     J = J.cpu().numpy()
     G = G.reshape(2, -1).cpu().numpy()
-    assert np.all(np.abs(J - J_ref) <= 1e-6 * np.abs(J_ref)), (J, J_ref)
     for p in range(2):
         assert rel(G[p], G_ref[p]) <= 1e-5, rel(G[p], G_ref[p])
+    assert np.all(np.abs(J - J_ref) <= J_TOL * np.abs(J_ref)), (J, J_ref)
+    # the FP64 reduction itself, on the GPU's own traces
+    tr = fwi.forward(_t(V)).double().cpu().numpy()
+    J_host = 0.5 * ((tr - d_obs.astype(np.float32)[None]) ** 2).sum(axis=(1, 2, 3)) / sigma ** 2
+    assert np.all(np.abs(J - J_host) <= 1e-10 * J_host), (J, J_host)
 
 
 def test_plain_loop_equals_batched_bit_for_bit():
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
     fwi = vg.Fwi.from_config(cfg, geo)
     Vt, Dt = _t(V), _t(d_obs)
+    # one cluster per particle (all sources in one work item) accumulates the
+    # sources in the same order as the plain loop
+    fwi.set_plan(0, 0, 0, g.nsrc)
     Jb, Gb = fwi.gradient(Vt, Dt, sigma)
     Sb = fwi.forward(Vt)
     fwi.set_mode(vg.FWI_MODE_PLAIN, 1)
@@ -72,6 +84,9 @@ def test_checkpoint_recompute_equals_store_all(K):
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
     fwi = vg.Fwi.from_config(cfg, geo)
     Vt, Dt = _t(V), _t(d_obs)
+    # all sources of a particle in one work item: the association the plain
+    # loop uses (splitting the sources over clusters only reorders the sum)
+    fwi.set_plan(0, 0, 0, g.nsrc)
     J1, G1 = fwi.gradient(Vt, Dt, sigma)
     G1 = G1.clone()
     fwi.set_mode(vg.FWI_MODE_BATCHED, K)
@@ -97,7 +112,7 @@ def test_ragged_grid_every_launch_shape_agrees_with_oracle():
         G = G.reshape(3, -1).cpu().numpy()
         for p in range(3):
             assert rel(G[p], G_ref[p]) <= 1e-5, (Q, Vr, T, p, rel(G[p], G_ref[p]))
-        assert np.all(np.abs(J.cpu().numpy() - J_ref) <= 1e-6 * J_ref)
+        assert np.all(np.abs(J.cpu().numpy() - J_ref) <= J_TOL * J_ref)
         if base is None:
             base = G
         else:
@@ -105,18 +120,33 @@ def test_ragged_grid_every_launch_shape_agrees_with_oracle():
 
 
 def test_autograd_backward_is_the_oracle_adjoint():
+    """FwiSeis backward (fwi_adjoint) for the misfit's own upstream
+    sensitivity equals fwi_gradient and the oracle; for a white-noise upstream
+    sensitivity the FP32 arithmetic floor is higher (an FP32 emulation of the
+    recurrence in numpy gives 2.4e-5 for one source), so 5e-5 holds there."""
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    J_ref, G_ref = cfg1_oracle_gradients(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    v = _t(V).reshape(2, cfg.nz, cfg.nx).requires_grad_(True)
+    seis = vg.FwiSeis.apply(v, fwi)
+    loss = 0.5 * (((seis - _t(d_obs)[None]) / sigma) ** 2).sum()
+    loss.backward()
+    got = v.grad.reshape(2, -1).cpu().numpy()
+    _, G = fwi.gradient(_t(V), _t(d_obs), sigma)
+    G = G.reshape(2, -1).cpu().numpy()
+    for p in range(2):
+        assert rel(got[p], G_ref[p]) <= 1e-5, rel(got[p], G_ref[p])
+        assert rel(got[p], G[p]) <= 1e-6, rel(got[p], G[p])
     rng = np.random.default_rng(12)
     dseis = rng.standard_normal((2, g.nsrc, g.nrec, g.nt))
     ref = np.stack([ofwi.adjoint_of_upstream(V[p], g, dseis[p]).reshape(-1)
                     for p in range(2)])
-    fwi = vg.Fwi.from_config(cfg, geo)
-    v = _t(V).reshape(2, cfg.nz, cfg.nx).requires_grad_(True)
+    v.grad = None
     seis = vg.FwiSeis.apply(v, fwi)
     (seis * _t(dseis)).sum().backward()
     got = v.grad.reshape(2, -1).cpu().numpy()
     for p in range(2):
-        assert rel(got[p], ref[p]) <= 1e-5, rel(got[p], ref[p])
+        assert rel(got[p], ref[p]) <= 5e-5, rel(got[p], ref[p])
 
 
 @pytest.mark.parametrize("prec,bound", [(vg.FWI_CKPT_BF16, 2e-2), (vg.FWI_CKPT_FP16, 5e-3)])
@@ -130,7 +160,7 @@ def test_reduced_precision_snapshots_error_is_bounded(prec, bound):
     print("snapshot precision %d: gradient rel-L2 %s" % (prec, errs))
     assert max(errs) <= bound
     # the misfit comes from the FP32 forward sweep and is unaffected
-    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= 1e-6 * J_ref)
+    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= J_TOL * J_ref)
 
 
 def test_noise_free_data_give_zero_misfit_and_gradient():
@@ -161,7 +191,7 @@ def test_single_particle_and_source_split_work_items():
     plan = fwi.query_plan(1)
     J, G = fwi.gradient(_t(V[:1]), _t(d_obs), sigma)
     assert rel(G.reshape(-1).cpu().numpy(), G_ref[0]) <= 1e-5
-    assert abs(J.item() - J_ref[0]) <= 1e-6 * J_ref[0]
+    assert abs(J.item() - J_ref[0]) <= J_TOL * J_ref[0]
     assert plan["sources_per_item"] >= 1
 
 
@@ -180,8 +210,7 @@ def test_full_size_cfg3_sampled_traces_and_gradient_direction():
     for p, s in ((0, 0), (1, 13)):
         ref = ofwi.forward(V[p].reshape(cfg.nz, cfg.nx), g, s)
         e = rel(seis[p, s].cpu().numpy(), ref)
-        # FP32 leapfrog round-off grows ~ sqrt(steps): 2000 steps
-        assert e <= 3e-5, (p, s, e)
+        assert e <= 1e-5, (p, s, e)
     # directional derivative at full size (property check, any size)
     obs = fwi.forward(_t(v_true)[None])[0].contiguous()
     sigma = 1e-3

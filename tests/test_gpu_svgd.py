@@ -43,7 +43,10 @@ def _unit_case(n, d, seed):
 def test_svgd_step_matches_oracle(gp, n, d):
     X, G = _unit_case(n, d, seed=n + d)
     Xt = _t(X)
-    eps = 0.3
+    # step size such that the update is O(1): the FP32 rounding of the new
+    # particles then does not mask the error of phi
+    phi0, _, _ = osvgd.svgd_direction(X, G)
+    eps = 0.5 / np.abs(phi0).max()
     ws, h2 = vg.svgd_step(Xt, _t(G), eps, gram_precision=gp)
     X_ref, h2_ref = osvgd.svgd_step(X, G, eps)
     assert rel(Xt.cpu().numpy(), X_ref) <= 1e-5
@@ -104,29 +107,38 @@ def test_median_selection_is_exact_on_exact_distances(n):
         med = allv[m // 2] if m % 2 else 0.5 * (allv[m // 2 - 1] + allv[m // 2])
         expect = 1.0 if med < 1e-30 else med / (2 * np.log(n + 1.0))
         assert abs(h2.item() - expect) <= 1e-14 * max(expect, 1.0)
-        assert np.allclose(D2, D2_ref, rtol=1e-5, atol=1e-4)
+        # centring makes the coordinates non-integer unless n is a power of
+        # two, so the one-piece BF16 image rounds them
+        # (the duplicated particle's zero distance is recovered from
+        # |x|^2 + |y|^2 - 2 x.y: its error scales with |x|^2, not with 0)
+        tol = 3e-3 if gp == vg.VIP_GRAM_BF16 else 1e-5
+        assert np.allclose(D2, D2_ref, rtol=tol, atol=tol * np.median(D2_ref))
 
 
 def test_bf16_gram_kernel_error_is_bounded():
+    """Velocity particles shaped like the batched workload (120 x 300 cells,
+    prior band of 2 km/s): squared distances and kernel values of the one-pass
+    BF16 Gram and of the three-piece split against the FP64 oracle."""
     cfg = synth.config("cfg3")
     v = synth.true_model(cfg)
     lo, hi = synth.prior_bounds(cfg, v)
-    X = synth.particles_from_prior(lo, hi, 64, seed=2)
-    rng = np.random.default_rng(1)
-    G = rng.standard_normal(X.shape) * 1e-3
-    out = {}
+    X = synth.particles_from_prior(lo, hi, 96, seed=2).astype(np.float32).astype(np.float64)
+    D2_ref = osvgd.pairwise_sqdist(X)
+    h2_ref = osvgd.median_bandwidth(D2_ref)
+    K_ref = osvgd.rbf(D2_ref, h2_ref)
+    off = ~np.eye(96, dtype=bool)
+    res = {}
     for gp in (vg.VIP_GRAM_BF16, vg.VIP_GRAM_BF16X3):
-        Xt = _t(X)
-        vg.svgd_step(Xt, _t(G), 1e3, gram_precision=gp)
-        out[gp] = Xt.double().cpu().numpy() - X.astype(np.float32)
-    X32 = X.astype(np.float32).astype(np.float64)
-    X_ref, _ = osvgd.svgd_step(X32, G.astype(np.float32).astype(np.float64), 1e3)
-    step_ref = X_ref - X32
-    e3 = rel(out[vg.VIP_GRAM_BF16X3], step_ref)
-    e1 = rel(out[vg.VIP_GRAM_BF16], step_ref)
-    print("update error: bf16x3 %.2e, bf16 %.2e" % (e3, e1))
-    assert e3 <= 1e-4
-    assert e1 <= 1e-2
+        D2, h2 = vg.svgd_sqdist(_t(X), gram_precision=gp)
+        D2 = D2.cpu().numpy()
+        eD = np.abs(D2 - D2_ref)[off].max() / np.median(D2_ref[off])
+        K = np.exp(-D2 / (2 * h2.item()))
+        eK = np.abs(K - K_ref).max() / K_ref[off].max()
+        res[gp] = (eD, eK, abs(h2.item() / h2_ref - 1))
+    print("one-pass BF16: D2 %.2e, Kbar %.2e, h2 %.2e; three-piece: D2 %.2e, Kbar %.2e, "
+          "h2 %.2e" % (res[0] + res[1]))
+    assert res[vg.VIP_GRAM_BF16][0] <= 1e-3 and res[vg.VIP_GRAM_BF16][1] <= 1e-3
+    assert res[vg.VIP_GRAM_BF16X3][0] <= 1e-6 and res[vg.VIP_GRAM_BF16X3][1] <= 1e-6
 
 
 def test_ssvgd_step_injected_noise_matches_oracle():
