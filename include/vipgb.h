@@ -210,6 +210,34 @@ int  svgd_step(float *X, const float *G, float gscale, int n, int d, float eps,
                void *ws, size_t ws_bytes, double *h2_used,
                vip_stream_t stream);
 
+/* svgd_step without a workspace argument and without any device memory
+ * allocation, for callers that cannot allocate GPU memory themselves: for
+ * example a plug-in that a host application calls with device pointers but
+ * no allocator, a process whose device memory is entirely owned by another
+ * framework's memory pool, or a latency-critical loop that must not call
+ * cudaMalloc/cudaFree (which can synchronise the device). The paper has no
+ * counterpart; this is a deployment variant of svgd_step.
+ *
+ * Scratch comes from one fixed array of VIP_NOALLOC_SCRATCH_BYTES (64 MiB)
+ * in device memory, reserved on every GPU that loads the library until the
+ * process exits. Problems whose svgd_workspace_size(n, d, gram_precision, 0)
+ * exceeds that size are rejected with VIP_ERR_NOMEM before any device call
+ * (with VIP_GRAM_BF16X3: n = 8 particles up to d = 76,928, n = 64 up to
+ * d = 61,184, n = 600 up to d = 7,953).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. All calls share the array and it keeps the
+ * previous call's contents: every call rewrites what it reads, so no state
+ * leaks between calls, but calls that overlap on the GPU (different
+ * streams, or host threads, without ordering between them) race on the
+ * scratch and give wrong results. Arguments and results are those of
+ * svgd_step. */
+#define VIP_NOALLOC_SCRATCH_BYTES (64u << 20)
+int  svgd_step_noalloc(float *X, const float *G, float gscale, int n, int d,
+                       float eps, float h2, const float *lo, const float *hi,
+                       int gram_precision, double *h2_used,
+                       vip_stream_t stream);
+
 /* Stochastic SVGD, Eq. (22) with the noise of Eq. (25):
  *   m_i <- clip(m_i + eps phi(m_i) + sqrt(2 eps / n) sum_j Lk_ij xi_j, lo, hi),
  * Lk the lower Cholesky factor of Kbar + tau I (Kbar_ij = k(m_i, m_j),

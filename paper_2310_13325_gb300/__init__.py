@@ -25,7 +25,7 @@ FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
 VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
 
 __all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "advi_sample", "advi_step",
-           "philox_normal", "svgd_workspace_size", "svgd_sqdist", "FWI_FP32", "FWI_CKPT_BF16",
+           "philox_normal", "svgd_workspace_size", "svgd_sqdist", "svgd_step_noalloc", "FWI_FP32", "FWI_CKPT_BF16",
            "FWI_CKPT_FP16", "FWI_MODE_BATCHED", "FWI_MODE_PLAIN", "VIP_GRAM_BF16",
            "VIP_GRAM_BF16X3", "VIP_GRAM_FP32", "VipError"]
 
@@ -251,6 +251,22 @@ def svgd_step(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GRAM_BF16X
                                 _ptr(ws), ws.numel(), _ptr(h2_used, torch.float64),
                                 _stream(stream)), "svgd_step")
     return ws, h2_used
+
+
+def svgd_step_noalloc(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GRAM_BF16X3,
+                      h2_used=None, gscale=1.0, stream=None):
+    """svgd_step whose scratch lives in the library's fixed device array
+    (VIP_NOALLOC_SCRATCH_BYTES) instead of a caller workspace, for callers that
+    cannot allocate device memory; no allocation happens inside the call.
+    Overlapping calls on the GPU share that array and must not run at once."""
+    torch = _torch()
+    n, d = X.shape
+    check(_lib.load().svgd_step_noalloc(_ptr(X, torch.float32, "X"),
+                                        _ptr(G, torch.float32, "G"), float(gscale), n, d,
+                                        float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
+                                        _ptr(hi, torch.float32, "hi"), int(gram_precision),
+                                        _ptr(h2_used, torch.float64), _stream(stream)),
+          "svgd_step_noalloc")
 
 
 def ssvgd_step(X, G, eps, seed, it, xi=None, h2=0.0, lo=None, hi=None,

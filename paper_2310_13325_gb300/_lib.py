@@ -45,6 +45,8 @@ _SIGS = {
                             c_size_t, c_void_p]),
     "svgd_step": (c_int, [c_void_p, c_void_p, c_float, c_int, c_int, c_float, c_float, c_void_p,
                           c_void_p, c_int, c_void_p, c_size_t, c_void_p, c_void_p]),
+    "svgd_step_noalloc": (c_int, [c_void_p, c_void_p, c_float, c_int, c_int, c_float, c_float,
+                                  c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "ssvgd_step": (c_int, [c_void_p, c_void_p, c_float, c_int, c_int, c_float, c_float, c_void_p,
                            c_void_p, c_int, c_void_p, c_size_t, c_void_p, c_uint64,
                            c_uint64, c_void_p, c_void_p, c_void_p]),

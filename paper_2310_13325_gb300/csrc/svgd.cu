@@ -24,6 +24,7 @@
 #include "philox.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace vip {
 
@@ -587,11 +588,55 @@ static int run_svgd(float *X, const float *G, float gscale, int n, int d, float 
   return VIP_OK;
 }
 
+// Scratch of svgd_step_noalloc: a fixed array in device memory that exists
+// for as long as the library is loaded, on every GPU that loads it. Host code
+// must not pass the symbol itself to a kernel (on the host it names a shadow
+// variable, not device memory): its device address is looked up once per
+// device with cudaGetSymbolAddress, with that device current.
+constexpr size_t kNoallocScratchBytes = (size_t)VIP_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128] = {};
+
+static int noalloc_scratch(void **out) {
+  int dev = -1;
+  VIP_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return VIP_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    VIP_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!p || ((uintptr_t)p & 255)) return VIP_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return VIP_OK;
+}
+
 }  // namespace vip
 
 using namespace vip;
 
 extern "C" {
+
+int svgd_step_noalloc(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
+                      const float *lo, const float *hi, int gram_precision, double *h2_used,
+                      vip_stream_t stream) {
+  if (!X || !G || n < 1 || d < 1 || !(eps >= 0.f) ||
+      (gram_precision != VIP_GRAM_BF16 && gram_precision != VIP_GRAM_BF16X3 &&
+       gram_precision != VIP_GRAM_FP32))
+    return VIP_ERR_ARG;
+  SvgdWs w;
+  // size check before any device call: oversize problems never touch the GPU
+  if (layout(n, d, gram_precision, 0, nullptr, 0, w) + 256 > kNoallocScratchBytes)
+    return VIP_ERR_NOMEM;
+  void *ws = nullptr;
+  int rc = noalloc_scratch(&ws);
+  if (rc) return rc;
+  return run_svgd(X, G, gscale, n, d, eps, h2, lo, hi, gram_precision, ws, kNoallocScratchBytes,
+                  h2_used, false, 0, 0, nullptr, nullptr, stream);
+}
 
 size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic) {
   if (n < 1 || d < 1) return 0;
