@@ -92,7 +92,9 @@ typedef struct fwi_ctx fwi_ctx;
 
 /* Execution modes. BATCHED: every (particle, source) pair of a call runs in
  * one persistent thread-block-cluster launch that keeps the wavefields in
- * shared memory for all time steps (replayed from a CUDA graph).
+ * shared memory for all time steps (replayed from a CUDA graph; setting the
+ * environment variable VIPGB_GRAPHS=0 before fwi_create launches the same
+ * kernels directly instead, e.g. under profilers).
  * PLAIN: one (particle, source) pair at a time, one kernel launch per time
  * step, wavefields in global memory, no graph - the comparison baseline. */
 #define FWI_MODE_BATCHED 0

@@ -7,6 +7,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -78,6 +79,7 @@ struct fwi_ctx {
   cudaStream_t last_stream = nullptr;
   std::map<std::tuple<int, int, int>, std::array<int, 3>> tuned;   // (P,mode,dtype) -> Q,V,T
   int force_Q = 0, force_V = 0, force_T = 0, force_spi = 0;          // launch override
+  int use_graphs = 1;   // VIPGB_GRAPHS=0 in the environment: eager launches
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
   int *pl_recmap = nullptr;
@@ -475,6 +477,12 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
       (uintptr_t)sigma_bits,
       ((uintptr_t)pl.Q << 32) | ((uintptr_t)pl.V << 16) | (uintptr_t)pl.T,
       ((uintptr_t)pl.ncl << 32) | (uintptr_t)pl.K};
+  if (!c->use_graphs) {
+    if ((rc = prepare_wave(pl))) return rc;
+    rc = enqueue_batched(c, pl, wp, P, sigma, misfit, st);
+    c->last_stream = st;
+    return rc;
+  }
   for (auto &g : c->graphs) {
     if (g.key == key) {
       VIP_TRY(cudaGraphLaunch(g.exec, st));
@@ -828,6 +836,7 @@ int fwi_create(const fwi_geom *g, size_t workspace_limit_bytes, fwi_ctx **out) {
     return fail(VIP_ERR_CUDA);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(VIP_ERR_CUDA);
+  if (const char *e = getenv("VIPGB_GRAPHS")) c->use_graphs = atoi(e) != 0;
   *out = c;
   return VIP_OK;
 }
