@@ -124,9 +124,9 @@ int  fwi_set_mode(fwi_ctx *ctx, int mode, int ckpt_every);
 int  fwi_autotune(fwi_ctx *ctx, int P, int precision);
 
 /* Force the batched launch shape: Q CTAs per cluster (1..16, 0 = any), V
- * rows per thread (4 or 8, 0 = any), T threads per CTA (multiple of 32,
+ * rows per thread (0 = any), T threads per CTA (multiple of 32,
  * 0 = any) and the number of sources one cluster processes per work item
- * (0 = any). All zeros restore automatic choice. A shape that does not fit
+ * (0 = any). V is one of 4, 5, 8, 10. All zeros restore automatic choice. A shape that does not fit
  * the device makes later calls return VIP_ERR_UNSUPPORTED. Traces and
  * misfits do not depend on the shape; gradients do not depend on Q, V, T
  * (every cell update and accumulation is evaluated identically) and are

@@ -48,8 +48,9 @@ struct Plan {
 struct Tables {
   int Q, V, Hb, NXg, ntask_pad;
   float *gz = nullptr, *gx = nullptr;
-  uint32_t *rmask = nullptr;
-  int *rbase = nullptr, *rperm = nullptr;
+  unsigned long long *rmask = nullptr;
+  int *rbase = nullptr, *rperm = nullptr, *rbstart = nullptr;
+  int rmax = 0;   // largest number of receivers in one band
 };
 
 struct GraphEntry {
@@ -103,9 +104,11 @@ static int band_height(int NZ, int Q, int V) {
   return idiv_up(h, V) * V;
 }
 
-static size_t wave_smem(int Hb, int PX, int NXg, bool grad) {
+static int receiver_pad(int R) { return (R + 3) & ~3; }
+
+static size_t wave_smem(int Hb, int PX, int NXg, bool grad, int R) {
   size_t f = 2 * (size_t)Hb * PX + PX + (grad ? 2 : 1) * (size_t)Hb * NXg * 4 +
-             ((Hb + 3) & ~3) + (size_t)NXg * 4;
+             ((Hb + 3) & ~3) + (size_t)NXg * 4 + 3 * (size_t)receiver_pad(R);
   return f * 4;
 }
 
@@ -126,7 +129,7 @@ static int get_tables(fwi_ctx *c, int Q, int V, Tables **out) {
   };
   for (int z = 0; z < c->NZ; ++z) gz[z] = prof(z, c->NZ);
   for (int x = 0; x < c->NX; ++x) gx[x] = prof(x, c->NX);
-  std::vector<uint32_t> mask((size_t)Q * t.ntask_pad, 0u);
+  std::vector<unsigned long long> mask((size_t)Q * t.ntask_pad, 0ull);
   std::vector<int> base((size_t)Q * t.ntask_pad, 0), perm(std::max(c->R, 1), 0);
   std::vector<std::array<long, 2>> order(c->R);
   for (int r = 0; r < c->R; ++r) {
@@ -142,17 +145,25 @@ static int get_tables(fwi_ctx *c, int Q, int V, Tables **out) {
     const long bt = key / 64;
     const int bit = (int)(key % 64);
     if (mask[bt] == 0) base[bt] = i;
-    mask[bt] |= 1u << bit;
+    mask[bt] |= 1ull << bit;
     perm[i] = (int)order[i][1];
   }
   VIP_TRY(cudaMalloc(&t.gz, gz.size() * 4));
   VIP_TRY(cudaMalloc(&t.gx, gx.size() * 4));
-  VIP_TRY(cudaMalloc(&t.rmask, mask.size() * 4));
+  VIP_TRY(cudaMalloc(&t.rmask, mask.size() * 8));
   VIP_TRY(cudaMalloc(&t.rbase, base.size() * 4));
   VIP_TRY(cudaMalloc(&t.rperm, perm.size() * 4));
+  std::vector<int> bstart(Q + 1, 0);
+  for (int i = 0; i < c->R; ++i) bstart[order[i][0] / 64 / t.ntask_pad + 1]++;
+  for (int b = 0; b < Q; ++b) {
+    t.rmax = std::max(t.rmax, bstart[b + 1]);
+    bstart[b + 1] += bstart[b];
+  }
+  VIP_TRY(cudaMalloc(&t.rbstart, bstart.size() * 4));
+  VIP_TRY(cudaMemcpy(t.rbstart, bstart.data(), bstart.size() * 4, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(t.gz, gz.data(), gz.size() * 4, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(t.gx, gx.data(), gx.size() * 4, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.rmask, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice));
+  VIP_TRY(cudaMemcpy(t.rmask, mask.data(), mask.size() * 8, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(t.rbase, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(t.rperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
   c->tables.push_back(t);
@@ -199,7 +210,7 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
 
 static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<Plan> &out) {
   const bool grad = mode != WM_FORWARD;
-  const int Vs[2] = {4, 8};
+  const int Vs[4] = {4, 5, 8, 10};
   for (int V : Vs) {
     const void *fn = kernel_ptr(V, mode, dtype);
     if (!fn) continue;
@@ -211,18 +222,22 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
       if (Hb < 4) continue;
       const int NXg = idiv_up(c->NX, 4);
       const int PX = 4 * (NXg + 2);
-      const size_t smem = wave_smem(Hb, PX, NXg, grad);
+      const size_t smem = wave_smem(Hb, PX, NXg, grad, c->R);
       if (smem + fa.sharedSizeBytes > c->smem_optin) continue;
       const int ntask = (Hb / V) * NXg;
       const int ntask_pad = idiv_up(ntask, 32) * 32;
-      int Ts[4] = {std::min(512, ntask_pad), idiv_up(idiv_up(ntask_pad, 2), 32) * 32,
+      // threads per CTA: whole numbers of tasks per thread (1, 2, 3) where
+      // possible, rounded up to warps, within the kernel's register budget
+      const int Tmax = wave_max_threads(V);
+      int Ts[4] = {ntask_pad, idiv_up(idiv_up(ntask_pad, 2), 32) * 32,
                    idiv_up(idiv_up(ntask_pad, 3), 32) * 32, c->force_T};
       for (int ti = 0; ti < 4; ++ti) {
-        if (Ts[ti] <= 0) continue;
-        const int T = std::min(512, std::max(64, Ts[ti]));
+        if (Ts[ti] <= 0 || Ts[ti] > Tmax) continue;
+        const int T = std::max(64, Ts[ti]);
         bool dup = false;
-        for (int tj = 0; tj < ti; ++tj) dup |= std::min(512, std::max(64, Ts[tj])) == T;
+        for (int tj = 0; tj < ti; ++tj) dup |= std::max(64, Ts[tj]) == T;
         if (dup) continue;
+        if (c->R > 4 * T) continue;   // receiver staging: at most 4 slots per thread
         Plan pl;
         pl.Q = Q; pl.V = V; pl.T = T; pl.Hb = Hb; pl.NXg = NXg; pl.PX = PX;
         pl.ntask = ntask; pl.ntask_pad = ntask_pad; pl.nwblk = ntask_pad / 32;
@@ -257,8 +272,10 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
           if (cost < best - 1e-9) { best = cost; pl.ipp = ipp2; pl.spi = spi; pl.items = items; }
         }
         pl.ncl = std::min(pl.items, ncl);
+        // per step: tasks per thread x (rows + ~3 rows of window warm-up)
+        // plus a fixed barrier cost
         const double tpt = (double)idiv_up(ntask_pad, T);
-        const double per_step = tpt * V + 6.0;
+        const double per_step = tpt * (V + 3.0) + 6.0;
         pl.est = best * per_step * (grad ? 2.0 : 1.0);
         out.push_back(pl);
       }
@@ -367,6 +384,7 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   wp.gz = tb->gz; wp.gx = tb->gx; wp.wavelet = c->d_wavelet;
   wp.src_z = c->d_src_z; wp.src_x = c->d_src_x;
   wp.rmask = tb->rmask; wp.rbase = tb->rbase; wp.rperm = tb->rperm;
+  wp.rbstart = tb->rbstart; wp.Rpad = receiver_pad(c->R);
   wp.items = pl.items; wp.ipp = pl.ipp; wp.spi = pl.spi;
   wp.K = pl.K; wp.nseg = pl.nseg;
   wp.status = c->d_status;
@@ -847,6 +865,7 @@ void fwi_destroy(fwi_ctx *c) {
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto &t : c->tables) {
     cudaFree(t.gz); cudaFree(t.gx); cudaFree(t.rmask); cudaFree(t.rbase); cudaFree(t.rperm);
+    cudaFree(t.rbstart);
   }
   cudaFree(c->scratch);
   cudaFree(c->d_wavelet); cudaFree(c->d_src_z); cudaFree(c->d_src_x); cudaFree(c->d_status);
@@ -865,7 +884,8 @@ int fwi_set_mode(fwi_ctx *c, int mode, int ckpt_every) {
 }
 
 int fwi_set_plan(fwi_ctx *c, int Q, int V, int T, int sources_per_item) {
-  if (!c || Q < 0 || Q > 16 || (V != 0 && V != 4 && V != 8) || T < 0 || T > 512 || (T % 32) ||
+  if (!c || Q < 0 || Q > 16 || (V != 0 && V != 4 && V != 5 && V != 8 && V != 10) || T < 0 ||
+      T > 512 || (T % 32) ||
       sources_per_item < 0)
     return VIP_ERR_ARG;
   c->force_Q = Q; c->force_V = V; c->force_T = T; c->force_spi = sources_per_item;

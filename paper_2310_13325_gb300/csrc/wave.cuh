@@ -63,9 +63,11 @@ struct WaveParams {
   const float *gx;       // [NXg*4] taper per padded column, 0 for dead columns
   const float *wavelet;  // [N] Ricker samples f(n dt)
   const int *src_z, *src_x;     // [S] padded source cell
-  const uint32_t *rmask; // [Q*ntask_pad] receivers in each thread task
+  const unsigned long long *rmask; // [Q*ntask_pad] receivers in each thread task
   const int *rbase;      // [Q*ntask_pad] first entry in rperm
   const int *rperm;      // [R] receiver numbers in task order
+  const int *rbstart;    // [Q+1] first rperm entry of each band
+  int Rpad;              // receiver slots per band in shared memory
   // work decomposition
   int P, items, ipp, spi;
   int K, nseg;           // restart-checkpoint interval, segments
@@ -96,10 +98,10 @@ template <class DT> struct Snap;
 template <> struct Snap<float> {
   static constexpr bool scaled = false;
   __device__ static void st(float *p, size_t i, float4 v, float) {
-    *reinterpret_cast<float4 *>(p + i) = v;
+    __stcg(reinterpret_cast<float4 *>(p + i), v);
   }
   __device__ static float4 ld(const float *p, size_t i, float) {
-    return *reinterpret_cast<const float4 *>(p + i);
+    return __ldcg(reinterpret_cast<const float4 *>(p + i));
   }
 };
 template <> struct Snap<__nv_bfloat16> {
@@ -113,7 +115,7 @@ template <> struct Snap<__nv_bfloat16> {
     *reinterpret_cast<uint2 *>(p + i) = u;
   }
   __device__ static float4 ld(const __nv_bfloat16 *p, size_t i, float) {
-    uint2 u = *reinterpret_cast<const uint2 *>(p + i);
+    uint2 u = __ldcg(reinterpret_cast<const uint2 *>(p + i));
     __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
     __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
     float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
@@ -131,7 +133,7 @@ template <> struct Snap<__half> {
     *reinterpret_cast<uint2 *>(p + i) = u;
   }
   __device__ static float4 ld(const __half *p, size_t i, float inv) {
-    uint2 u = *reinterpret_cast<const uint2 *>(p + i);
+    uint2 u = __ldcg(reinterpret_cast<const uint2 *>(p + i));
     __half2 a = *reinterpret_cast<__half2 *>(&u.x);
     __half2 b = *reinterpret_cast<__half2 *>(&u.y);
     float2 fa = __half22float2(a), fb = __half22float2(b);
@@ -180,24 +182,38 @@ __device__ __forceinline__ float update_cell(float g, float w, float s, float u,
 // Batched persistent cluster kernel.
 struct Band {
   float *U[2];                 // local field buffers [Hb][PX]
-  const float *up[2], *dn[2];  // neighbours' buffers (generic) or zero row
-  const float *Zr;             // one row of zeros
+  uint32_t su[2];              // their shared-window addresses
+  uint32_t sup[2], sdn[2];     // neighbours' buffers in the cluster window
+  bool has_up, has_dn;         // whether the band has a neighbour above / below
+  uint32_t szr;                // address of one row of zeros
   float *W;                    // [Hb][NXg*4] w'
   float *Gm;                   // [Hb][NXg*4] gradient accumulator
   float *gzs;                  // [Hb]
   float *gxs;                  // [NXg*4]
+  int *rid;                    // [Rpad] receiver numbers of this band (rperm order)
+  float *val;                  // [2][Rpad] per-receiver values of the next two steps
+  int rb0, nrb;                // first rperm entry and number of receivers of the band
   int b;
 };
 
-// Row rr (band-local, -4 <= rr < Hb + 4) of the current level: own rows from
-// shared memory, the 4 rows beyond either band edge from the neighbouring
-// CTA (distributed shared memory) or zeros at the grid boundary.
-__device__ __forceinline__ const float *band_row(const float *cur, const float *up,
-                                                 const float *dn, const float *Zr,
-                                                 int rr, int Hb, int PX) {
-  if (rr < 0) return up == Zr ? Zr : up + (rr + Hb) * PX;
-  if (rr >= Hb) return dn == Zr ? Zr : dn + (rr - Hb) * PX;
-  return cur + rr * PX;
+// 16-byte load from the cluster's shared-memory window (own CTA or a
+// neighbour), 32-bit address.
+__device__ __forceinline__ float4 ld_cluster4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t cta_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(cta_addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
 // Per-step context of the cell loop.
@@ -212,138 +228,273 @@ struct StepArgs {
   bool record;       // forward: write traces / residuals
   size_t dofs;       // element offset of this step's snapshot slab
   size_t sofs;       // offset of this step's scale slab
+  long long dnext;   // adjoint: element offset of the next step's slab (-1: none)
+  int vnext_t;       // trace sample whose receiver values the next step uses (-1: none)
   double *Jacc;      // per-thread squared-residual accumulator
 };
 
+// Receiver mask type of a task (4 bits per row).
+template <int V> struct MaskT { using type = uint32_t; };
+template <> struct MaskT<10> { using type = unsigned long long; };
+
+// Per-task constants of one step.
+struct TaskCtx {
+  const float *crow;   // current level, row r0, column group (shared)
+  float *nrow;         // next level, row r0
+  const float *wrow;   // w', row r0
+  float *grow;         // accumulator, row r0
+  const float *gz;     // taper, row r0
+  float4 gx4;
+  bool xin;            // all four columns outside the sponge
+  bool valid;
+  int srow, slane;     // source row within the task (-1: none) and lane
+  int rb;              // band-local index of the task's first receiver
+  int r0, gcol;
+};
+
+template <int V, bool ADJ, bool SNAP, int MODE, class DT>
+__device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, const StepArgs &a,
+                                          const TaskCtx &c, typename MaskT<V>::type rm,
+                                          DT *Dtask, const DT *Dnext, const float *Stask,
+                                          float *Sw, const float *vcur, uint32_t up_s,
+                                          uint32_t dn_s, uint32_t cur_s, bool edge, int tid) {
+  using M = typename MaskT<V>::type;
+  const int PX = p.PX, W4 = p.NXg * 4, Hb = p.Hb;
+  const uint32_t rowb = (uint32_t)PX * 4u;
+  // adjoint: snapshot rows are loaded two rows ahead of their use
+  float4 dq[V];
+  float dinv[V];
+  if (ADJ && SNAP) {
+#pragma unroll
+    for (int i = 0; i < 2 && i < V; ++i) {
+      dinv[i] = Snap<DT>::scaled ? Stask[i] : 1.f;
+      dq[i] = Snap<DT>::ld(Dtask, (size_t)i * W4, 1.f);
+    }
+  }
+  // the 9-row vertical window: rows r0-4 .. r0+3 first. Strips away from
+  // the band edges read their own rows; edge strips map each row to the
+  // neighbouring band or the zero row.
+  const uint32_t colb = (uint32_t)(c.gcol + 4) * 4u;
+  const uint32_t wb = cur_s + (uint32_t)(c.r0 - 4) * rowb + colb;
+  auto wrow_addr = [&](int i) -> uint32_t {
+    if (!edge) return wb + (uint32_t)i * rowb;
+    const int rr = c.r0 - 4 + i;
+    if (rr < 0) return B.has_up ? up_s + (uint32_t)(rr + Hb) * rowb + colb : B.szr + colb;
+    if (rr >= Hb) return B.has_dn ? dn_s + (uint32_t)(rr - Hb) * rowb + colb : B.szr + colb;
+    return wb + (uint32_t)i * rowb;
+  };
+  float4 win[9];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) win[i] = ld_cluster4(wrow_addr(i));
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    if (ADJ && SNAP && i + 2 < V) {
+      dinv[i + 2] = Snap<DT>::scaled ? Stask[i + 2] : 1.f;
+      dq[i + 2] = Snap<DT>::ld(Dtask, (size_t)(i + 2) * W4, 1.f);
+    }
+    win[8] = ld_cluster4(wrow_addr(i + 8));
+    const float *rp = c.crow + i * PX;
+    const float4 Lf = ld4(rp - 4), Rf = ld4(rp + 4), C = win[4];
+    const float hrow[12] = {Lf.x, Lf.y, Lf.z, Lf.w, C.x, C.y, C.z, C.w,
+                            Rf.x, Rf.y, Rf.z, Rf.w};
+    float s4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float h[8], vv[8];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        h[k] = hrow[j + k];          // offsets -4..-1
+        h[4 + k] = hrow[j + 5 + k];  // offsets +1..+4
+        vv[k] = comp(win[k], j);
+        vv[4 + k] = comp(win[5 + k], j);
+      }
+      s4[j] = lap_cell(p, hrow[4 + j], h, vv);
+    }
+    const uint32_t rbits = (uint32_t)(rm >> (4 * i)) & 0xFu;
+    if (!ADJ) {
+      if (c.srow == i) s4[c.slane] = __fadd_rn(s4[c.slane], a.src_val);
+    } else if (MODE != WM_FORWARD && rbits) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (rbits & (1u << j)) {
+          const int lr = c.rb + __popcll((unsigned long long)(rm & (((M)1 << (4 * i + j)) - 1)));
+          s4[j] = __fadd_rn(s4[j], vcur[lr]);
+        }
+      }
+    }
+    const float4 Wv = ld4(c.wrow + i * W4);
+    const float gzr = c.gz[i];
+    float *np_ = c.nrow + i * PX;
+    const float4 AP = ld4(np_);
+    float4 an;
+    if (c.xin && gzr == 1.f) {
+      // outside the sponge g = 1: the general update reduces exactly to this
+      an.x = __fsub_rn(__fmaf_rn(Wv.x, s4[0], __fadd_rn(C.x, C.x)), AP.x);
+      an.y = __fsub_rn(__fmaf_rn(Wv.y, s4[1], __fadd_rn(C.y, C.y)), AP.y);
+      an.z = __fsub_rn(__fmaf_rn(Wv.z, s4[2], __fadd_rn(C.z, C.z)), AP.z);
+      an.w = __fsub_rn(__fmaf_rn(Wv.w, s4[3], __fadd_rn(C.w, C.w)), AP.w);
+    } else {
+      an.x = update_cell(__fmul_rn(gzr, c.gx4.x), Wv.x, s4[0], C.x, AP.x);
+      an.y = update_cell(__fmul_rn(gzr, c.gx4.y), Wv.y, s4[1], C.y, AP.y);
+      an.z = update_cell(__fmul_rn(gzr, c.gx4.z), Wv.z, s4[2], C.z, AP.z);
+      an.w = update_cell(__fmul_rn(gzr, c.gx4.w), Wv.w, s4[3], C.w, AP.w);
+    }
+    if (c.valid) st4(np_, an);
+    if (SNAP) {
+      const float4 sv = make_float4(s4[0], s4[1], s4[2], s4[3]);
+      if (!ADJ) {
+        float mul = 1.f;
+        if (Snap<DT>::scaled) {
+          float m = c.valid ? fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)),
+                                    fmaxf(fabsf(sv.z), fabsf(sv.w)))
+                            : 0.f;
+          m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+          int e = 0;
+          if (m > 0.f) { frexpf(m, &e); e = 15 - e; }
+          e = max(-120, min(120, e));
+          mul = ldexpf(1.f, e);
+          if ((tid & 31) == 0) Sw[i] = ldexpf(1.f, -e);
+        }
+        if (c.valid) Snap<DT>::st(Dtask, (size_t)i * W4, sv, mul);
+      } else if (c.valid) {
+        const float4 dv = dq[i];
+        const float inv = dinv[i];
+        float *gp = c.grow + i * W4;
+        float4 gm = ld4(gp);
+        gm.x = __fmaf_rn(an.x, Snap<DT>::scaled ? dv.x * inv : dv.x, gm.x);
+        gm.y = __fmaf_rn(an.y, Snap<DT>::scaled ? dv.y * inv : dv.y, gm.y);
+        gm.z = __fmaf_rn(an.z, Snap<DT>::scaled ? dv.z * inv : dv.z, gm.z);
+        gm.w = __fmaf_rn(an.w, Snap<DT>::scaled ? dv.w * inv : dv.w, gm.w);
+        st4(gp, gm);
+      }
+    }
+    if (!ADJ && a.record && rbits) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (rbits & (1u << j)) {
+          const int lr = c.rb + __popcll((unsigned long long)(rm & (((M)1 << (4 * i + j)) - 1)));
+          const int rr = B.rid[lr];
+          const float d = comp(an, j);
+          if (MODE == WM_FORWARD) {
+            p.seis[((size_t)a.pair * p.R + rr) * p.N + a.t] = d;
+          } else if (MODE == WM_GRADIENT) {
+            const double res = (double)d - (double)vcur[lr];
+            *a.Jacc = __fma_rn(res, res, *a.Jacc);
+            p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + a.t] =
+                (float)(res * (double)p.rho_scale);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) win[k] = win[k + 1];
+  }
+  // adjoint: pull the next step's snapshot rows of this task towards L2
+  if (ADJ && SNAP && Dnext && c.valid) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) prefetch_l2(Dnext + (size_t)i * W4);
+  }
+}
+
+// One time step of the band: every thread updates its tasks (4 adjacent
+// cells x V rows). Window rows come from the CTA's own shared memory, or for
+// the strips at either band edge from the cluster's shared-memory window
+// (neighbouring bands, or the zero row at the grid boundary).
 template <int V, bool ADJ, bool SNAP, int MODE, class DT>
 __device__ __forceinline__ void band_step(const WaveParams &p, const Band &B,
                                           const StepArgs &a, int tid, int T) {
+  using M = typename MaskT<V>::type;
   const int Hb = p.Hb, PX = p.PX, NXg = p.NXg, W4 = NXg * 4;
   const float *cur = a.ph ? B.U[1] : B.U[0];
   float *nxt = a.ph ? B.U[0] : B.U[1];
-  const float *up = a.ph ? B.up[1] : B.up[0];
-  const float *dn = a.ph ? B.dn[1] : B.dn[0];
-  const float *Zr = B.Zr;
+  const uint32_t cur_s = a.ph ? B.su[1] : B.su[0];
+  const uint32_t up_s = a.ph ? B.sup[1] : B.sup[0];
+  const uint32_t dn_s = a.ph ? B.sdn[1] : B.sdn[0];
   DT *Dp = reinterpret_cast<DT *>(p.Dbuf) + a.slot * p.Dslot + a.dofs;
+  const DT *Dn = a.dnext >= 0 ? reinterpret_cast<const DT *>(p.Dbuf) + a.slot * p.Dslot + a.dnext
+                              : nullptr;
   float *Sp = Snap<DT>::scaled ? p.Dscale + a.slot * p.DSslot + a.sofs : nullptr;
+  const float *vcur = B.val + (a.t & 1) * p.Rpad;
+  // receiver values of the next step are fetched now and parked in shared
+  // memory at the end of this step, so no dependent global load sits on the
+  // critical path of the receiver rows
+  float vnext[4];
+  const bool fetch = a.vnext_t >= 0;
+  if (fetch) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = tid + u * T;
+      if (q < B.nrb) {
+        const int rr = B.rid[q];
+        if (!ADJ)
+          vnext[u] = __ldg(&p.dobs[((size_t)a.s * p.R + rr) * p.N + a.vnext_t]);
+        else if (MODE == WM_GRADIENT)
+          vnext[u] = p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + a.vnext_t];
+        else
+          vnext[u] = __fmul_rn(p.rho_scale,
+                               __ldg(&p.dseis[((size_t)a.pair * p.R + rr) * p.N + a.vnext_t]));
+      }
+    }
+  }
+  const int nstrip = Hb / V;
   for (int task0 = tid; task0 < p.ntask_pad; task0 += T) {
-    const bool valid = task0 < p.ntask;
-    const int task = valid ? task0 : p.ntask - 1;
+    TaskCtx c;
+    c.valid = task0 < p.ntask;
+    const int task = c.valid ? task0 : p.ntask - 1;
     const int sp = task / NXg;
     const int cgp = task - sp * NXg;
-    const int r0 = sp * V;
-    const int col = (cgp + 1) * 4;
-    const int gcol = cgp * 4;
-    const float4 gx4 = ld4(B.gxs + gcol);
-    uint32_t rm = 0;
-    int rb = 0;
+    c.r0 = sp * V;
+    c.gcol = cgp * 4;
+    const int col = c.gcol + 4;
+    c.crow = cur + c.r0 * PX + col;
+    c.nrow = nxt + c.r0 * PX + col;
+    c.wrow = B.W + c.r0 * W4 + c.gcol;
+    c.grow = B.Gm + c.r0 * W4 + c.gcol;
+    c.gz = B.gzs + c.r0;
+    c.gx4 = ld4(B.gxs + c.gcol);
+    c.xin = c.gx4.x == 1.f && c.gx4.y == 1.f && c.gx4.z == 1.f && c.gx4.w == 1.f;
+    M rm = 0;
+    c.rb = 0;
     if ((!ADJ && a.record) || (ADJ && MODE != WM_FORWARD)) {
-      rm = valid ? p.rmask[B.b * p.ntask_pad + task] : 0u;
-      rb = p.rbase[B.b * p.ntask_pad + task];
+      rm = c.valid ? (M)__ldg(&p.rmask[B.b * p.ntask_pad + task]) : (M)0;
+      c.rb = __ldg(&p.rbase[B.b * p.ntask_pad + task]) - B.rb0;   // band-local
     }
-    float4 win[9];
+    c.srow = (!ADJ && c.valid && task == a.src_task) ? (a.src_bit >> 2) : -1;
+    c.slane = a.src_bit & 3;
+    const size_t toff = (size_t)c.r0 * W4 + c.gcol;
+    DT *Dt = Dp + toff;
+    const DT *Dnt = Dn ? Dn + toff : nullptr;
+    const float *St = Sp ? Sp + (task0 / 32) * V : nullptr;
+    float *Sw = Sp ? Sp + (task0 / 32) * V : nullptr;
+    const bool edge = (sp == 0) || (sp == nstrip - 1);
+    task_rows<V, ADJ, SNAP, MODE, DT>(p, B, a, c, rm, Dt, Dnt, St, Sw, vcur, up_s, dn_s, cur_s,
+                                      edge, tid);
+  }
+  // forward step n feeds step n+1, adjoint step k feeds step k-1: both have
+  // the parity of t+1
+  if (fetch) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) win[i] = ld4(band_row(cur, up, dn, Zr, r0 - 4 + i, Hb, PX) + col);
-#pragma unroll
-    for (int i = 0; i < V; ++i) {
-      const int r = r0 + i;
-      win[8] = ld4(band_row(cur, up, dn, Zr, r + 4, Hb, PX) + col);
-      const float *rp = cur + r * PX + col;
-      const float4 Lf = ld4(rp - 4), Rf = ld4(rp + 4), C = win[4];
-      const float hrow[12] = {Lf.x, Lf.y, Lf.z, Lf.w, C.x, C.y, C.z, C.w,
-                              Rf.x, Rf.y, Rf.z, Rf.w};
-      float s4[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float h[8], vv[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          h[k] = hrow[j + k];          // offsets -4..-1
-          h[4 + k] = hrow[j + 5 + k];  // offsets +1..+4
-          vv[k] = comp(win[k], j);
-          vv[4 + k] = comp(win[5 + k], j);
-        }
-        s4[j] = lap_cell(p, hrow[4 + j], h, vv);
-      }
-      const uint32_t rbits = (rm >> (4 * i)) & 0xFu;
-      if (!ADJ) {
-        if (task == a.src_task && valid && (a.src_bit >> 2) == i)
-          s4[a.src_bit & 3] = __fadd_rn(s4[a.src_bit & 3], a.src_val);
-      } else if (MODE != WM_FORWARD && rbits) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (rbits & (1u << j)) {
-            const int rr = p.rperm[rb + __popc(rm & ((1u << (4 * i + j)) - 1u))];
-            float val;
-            if (MODE == WM_GRADIENT)
-              val = p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + (a.t - 1)];
-            else
-              val = __fmul_rn(p.rho_scale,
-                              p.dseis[((size_t)a.pair * p.R + rr) * p.N + (a.t - 1)]);
-            s4[j] = __fadd_rn(s4[j], val);
-          }
-        }
-      }
-      const size_t cell = (size_t)r * W4 + gcol;
-      const float4 Wv = ld4(B.W + cell);
-      const float gzr = B.gzs[r];
-      const float4 AP = ld4(nxt + r * PX + col);
-      float4 an;
-      an.x = update_cell(__fmul_rn(gzr, gx4.x), Wv.x, s4[0], C.x, AP.x);
-      an.y = update_cell(__fmul_rn(gzr, gx4.y), Wv.y, s4[1], C.y, AP.y);
-      an.z = update_cell(__fmul_rn(gzr, gx4.z), Wv.z, s4[2], C.z, AP.z);
-      an.w = update_cell(__fmul_rn(gzr, gx4.w), Wv.w, s4[3], C.w, AP.w);
-      if (valid) st4(nxt + r * PX + col, an);
-      if (SNAP) {
-        const float4 sv = make_float4(s4[0], s4[1], s4[2], s4[3]);
-        if (!ADJ) {
-          float mul = 1.f;
-          if (Snap<DT>::scaled) {
-            float m = valid ? fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)),
-                                    fmaxf(fabsf(sv.z), fabsf(sv.w)))
-                            : 0.f;
-            m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-            int e = 0;
-            if (m > 0.f) { frexpf(m, &e); e = 15 - e; }
-            e = max(-120, min(120, e));
-            mul = ldexpf(1.f, e);
-            if ((tid & 31) == 0) Sp[(task0 / 32) * V + i] = ldexpf(1.f, -e);
-          }
-          if (valid) Snap<DT>::st(Dp, cell, sv, mul);
-        } else {
-          const float inv = Snap<DT>::scaled ? Sp[(task0 / 32) * V + i] : 1.f;
-          const float4 dv = Snap<DT>::ld(Dp, cell, inv);
-          if (valid) {
-            float4 gm = ld4(B.Gm + cell);
-            gm.x = __fmaf_rn(an.x, dv.x, gm.x);
-            gm.y = __fmaf_rn(an.y, dv.y, gm.y);
-            gm.z = __fmaf_rn(an.z, dv.z, gm.z);
-            gm.w = __fmaf_rn(an.w, dv.w, gm.w);
-            st4(B.Gm + cell, gm);
-          }
-        }
-      }
-      if (!ADJ && a.record && rbits) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (rbits & (1u << j)) {
-            const int rr = p.rperm[rb + __popc(rm & ((1u << (4 * i + j)) - 1u))];
-            const float d = comp(an, j);
-            if (MODE == WM_FORWARD) {
-              p.seis[((size_t)a.pair * p.R + rr) * p.N + a.t] = d;
-            } else if (MODE == WM_GRADIENT) {
-              const double res =
-                  (double)d - (double)p.dobs[((size_t)a.s * p.R + rr) * p.N + a.t];
-              *a.Jacc = __fma_rn(res, res, *a.Jacc);
-              p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + a.t] =
-                  (float)(res * (double)p.rho_scale);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) win[k] = win[k + 1];
-    }
+    for (int u = 0; u < 4; ++u)
+      if (tid + u * T < B.nrb) B.val[((a.t + 1) & 1) * p.Rpad + tid + u * T] = vnext[u];
+  }
+}
+
+// Value used at the receivers in the first step of a sweep (before the
+// per-step prefetch takes over): dobs at sample t (forward) or the adjoint
+// source at sample t (adjoint), into slot `par`.
+template <bool ADJ, int MODE>
+__device__ __forceinline__ void receiver_values(const WaveParams &p, const Band &B, int tid,
+                                                int slot, int s, int pair, int t, int par) {
+  for (int q = tid; q < B.nrb; q += blockDim.x) {
+    const int rr = B.rid[q];
+    float v;
+    if (!ADJ)
+      v = p.dobs[((size_t)s * p.R + rr) * p.N + t];
+    else if (MODE == WM_GRADIENT)
+      v = p.rho[slot * p.rhoslot + (size_t)rr * p.N + t];
+    else
+      v = __fmul_rn(p.rho_scale, p.dseis[((size_t)pair * p.R + rr) * p.N + t]);
+    B.val[par * p.Rpad + q] = v;
   }
 }
 
@@ -370,8 +521,12 @@ __device__ __forceinline__ void band_zero(const WaveParams &p, const Band &B, in
   for (int q = tid; q < n / 4; q += T) st4(B.U[0] + 4 * q, make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
+// Threads per CTA allowed for V rows per thread (register budget).
+template <int V> struct WaveMaxThreads { static constexpr int value = V >= 8 ? 448 : 512; };
+
 template <int V, int MODE, class DT>
-__global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_constant__ WaveParams p) {
+__global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
+    wave_cluster_kernel(const __grid_constant__ WaveParams p) {
   cg::cluster_group cluster = cg::this_cluster();
   const int b = (int)cluster.block_rank();
   const int cid = blockIdx.x / p.Q;
@@ -385,14 +540,22 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
   B.U[0] = smem;
   B.U[1] = smem + HP;
   float *Zr = smem + 2 * HP;
-  B.Zr = Zr;
   B.W = Zr + p.PX;
   B.Gm = B.W + HW;
   B.gzs = B.Gm + (MODE != WM_FORWARD ? HW : 0);
   B.gxs = B.gzs + ((p.Hb + 3) & ~3);
+  B.rid = reinterpret_cast<int *>(B.gxs + p.NXg * 4);
+  B.val = reinterpret_cast<float *>(B.rid + p.Rpad);
+  B.rb0 = p.rbstart[b];
+  B.nrb = p.rbstart[b + 1] - B.rb0;
+  for (int q = tid; q < B.nrb; q += T) B.rid[q] = p.rperm[B.rb0 + q];
+  B.szr = (uint32_t)__cvta_generic_to_shared(Zr);
+  B.has_up = b > 0;
+  B.has_dn = b < p.Q - 1;
   for (int ph = 0; ph < 2; ++ph) {
-    B.up[ph] = b > 0 ? cluster.map_shared_rank(B.U[ph], b - 1) : Zr;
-    B.dn[ph] = b < p.Q - 1 ? cluster.map_shared_rank(B.U[ph], b + 1) : Zr;
+    B.su[ph] = (uint32_t)__cvta_generic_to_shared(B.U[ph]);
+    B.sup[ph] = B.has_up ? cluster_addr(B.su[ph], (uint32_t)(b - 1)) : 0u;
+    B.sdn[ph] = B.has_dn ? cluster_addr(B.su[ph], (uint32_t)(b + 1)) : 0u;
   }
   for (int q = tid; q < p.PX; q += T) Zr[q] = 0.f;
   for (int q = tid; q < p.Hb; q += T) B.gzs[q] = p.gz[b * p.Hb + q];
@@ -437,19 +600,22 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
       }
       // ---------------- forward sweep
       band_zero(p, B, tid, T);
+      if (MODE == WM_GRADIENT) receiver_values<false, MODE>(p, B, tid, cid, s, pair, 0, 0);
       cluster.sync();
       double jacc = 0.0;
       int ph = 0;
       for (int n = 0; n < p.N; ++n) {
         StepArgs a;
         a.ph = ph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
-        a.src_task = src_task; a.src_bit = src_bit; a.src_val = p.wavelet[n];
-        a.record = true; a.Jacc = &jacc;
+        a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
+        a.record = true; a.Jacc = &jacc; a.dnext = -1;
+        a.vnext_t = (MODE == WM_GRADIENT && n + 1 < p.N) ? n + 1 : -1;
         if (MODE == WM_FORWARD || p.K > 1) {
-          if (MODE != WM_FORWARD && n % p.K == 0)
+          if (MODE != WM_FORWARD && n % p.K == 0) {
             band_copy(p, B, ph, p.CK + cid * p.CKslot + (size_t)(n / p.K) * 2 * slab +
                                     (size_t)b * 2 * p.Hb * W4, true, tid, T);
-          __syncthreads();   // the copy and the step map cells to threads differently
+            __syncthreads();   // the copy and the step map cells to threads differently
+          }
           a.dofs = 0; a.sofs = 0;
           band_step<V, false, false, MODE, DT>(p, B, a, tid, T);
         } else {
@@ -478,6 +644,7 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
 
       // ---------------- adjoint sweep
       band_zero(p, B, tid, T);
+      if (p.K == 1) receiver_values<true, MODE>(p, B, tid, cid, s, pair, p.N - 1, p.N & 1);
       cluster.sync();
       ph = 0;
       if (p.K == 1) {
@@ -487,6 +654,8 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
           a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jacc = nullptr;
           a.dofs = (size_t)(k - 1) * slab + (size_t)b * p.Hb * W4;
           a.sofs = ((size_t)(k - 1) * p.Q + b) * p.nwblk * V;
+          a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * p.Hb * W4) : -1;
+          a.vnext_t = k >= 2 ? k - 2 : -1;
           band_step<V, true, true, MODE, DT>(p, B, a, tid, T);
           cluster.sync();
           ph ^= 1;
@@ -504,8 +673,8 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
           for (int n = n0; n < n1; ++n) {              // recompute the segment
             StepArgs a;
             a.ph = fph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
-            a.src_task = src_task; a.src_bit = src_bit; a.src_val = p.wavelet[n];
-            a.record = false; a.Jacc = nullptr;
+            a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
+            a.record = false; a.Jacc = nullptr; a.dnext = -1; a.vnext_t = -1;
             a.dofs = (size_t)(n - n0) * slab + (size_t)b * p.Hb * W4;
             a.sofs = ((size_t)(n - n0) * p.Q + b) * p.nwblk * V;
             band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
@@ -513,6 +682,7 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
             fph ^= 1;
           }
           band_copy(p, B, 0, AS, false, tid, T);       // restore the adjoint state
+          receiver_values<true, MODE>(p, B, tid, cid, s, pair, n1 - 1, n1 & 1);
           ph = 0;
           cluster.sync();
           for (int k = n1; k > n0; --k) {
@@ -521,6 +691,10 @@ __global__ void __launch_bounds__(512, 1) wave_cluster_kernel(const __grid_const
             a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jacc = nullptr;
             a.dofs = (size_t)(k - 1 - n0) * slab + (size_t)b * p.Hb * W4;
             a.sofs = ((size_t)(k - 1 - n0) * p.Q + b) * p.nwblk * V;
+            a.dnext = k - 2 >= n0 ? (long long)((size_t)(k - 2 - n0) * slab +
+                                                (size_t)b * p.Hb * W4)
+                                  : -1;
+            a.vnext_t = k - 1 > n0 ? k - 2 : -1;
             band_step<V, true, true, MODE, DT>(p, B, a, tid, T);
             cluster.sync();
             ph ^= 1;

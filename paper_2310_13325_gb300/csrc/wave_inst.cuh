@@ -10,6 +10,10 @@ namespace vip {
 const void *wave_kernel_f32(int V, int mode);
 const void *wave_kernel_bf16(int V, int mode);
 const void *wave_kernel_f16(int V, int mode);
+const void *wave_kernel_fwd(int V);
+
+// Largest CTA size the kernel for V rows per thread is built for.
+inline int wave_max_threads(int V) { return V >= 8 ? 448 : 512; }
 
 template <class DT>
 const void *wave_kernel_table(int V, int mode) {
@@ -17,7 +21,9 @@ const void *wave_kernel_table(int V, int mode) {
   if (V == VV && mode == MM)                                           \
     return reinterpret_cast<const void *>(&wave_cluster_kernel<VV, MM, DT>);
   VIP_K(4, WM_GRADIENT) VIP_K(4, WM_ADJOINT)
+  VIP_K(5, WM_GRADIENT) VIP_K(5, WM_ADJOINT)
   VIP_K(8, WM_GRADIENT) VIP_K(8, WM_ADJOINT)
+  VIP_K(10, WM_GRADIENT) VIP_K(10, WM_ADJOINT)
 #undef VIP_K
   return nullptr;
 }
