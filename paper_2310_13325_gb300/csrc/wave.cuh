@@ -178,6 +178,50 @@ __device__ __forceinline__ float update_cell(float g, float w, float s, float u,
   return __fmul_rn(g, __fmaf_rn(-g, ap, t));
 }
 
+// Packed FP32 pairs (two cells per instruction, each lane rounded exactly as
+// the scalar operation of the same name).
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+  return *reinterpret_cast<unsigned long long *>(&a);
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+  return *reinterpret_cast<float2 *>(&r);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+  return upk(r);
+}
+
+// Laplacian bracket of the cell pair (j, j+1): lf[k], rt[k] the neighbours at
+// distance k+1 to the left and right, up[k], dn[k] above and below; same
+// operation order per lane as lap_cell.
+__device__ __forceinline__ float2 lap_pair(const WaveParams &p, float2 u, const float2 lf[4],
+                                           const float2 rt[4], const float2 up[4],
+                                           const float2 dn[4]) {
+  const float2 u4 = mul2(make_float2(4.f, 4.f), u);
+  float2 s = mul2(make_float2(p.c4, p.c4),
+                  sub2(add2(add2(lf[3], rt[3]), add2(up[3], dn[3])), u4));
+  s = fma2(make_float2(p.c3, p.c3), sub2(add2(add2(lf[2], rt[2]), add2(up[2], dn[2])), u4), s);
+  s = fma2(make_float2(p.c2, p.c2), sub2(add2(add2(lf[1], rt[1]), add2(up[1], dn[1])), u4), s);
+  s = fma2(make_float2(p.c1, p.c1), sub2(add2(add2(lf[0], rt[0]), add2(up[0], dn[0])), u4), s);
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // Batched persistent cluster kernel.
 struct Band {
@@ -295,24 +339,34 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
     win[8] = ld_cluster4(wrow_addr(i + 8));
     const float *rp = c.crow + i * PX;
     const float4 Lf = ld4(rp - 4), Rf = ld4(rp + 4), C = win[4];
-    const float hrow[12] = {Lf.x, Lf.y, Lf.z, Lf.w, C.x, C.y, C.z, C.w,
-                            Rf.x, Rf.y, Rf.z, Rf.w};
-    float s4[4];
+    // cell pairs (0,1) and (2,3): neighbours at distance 1..4
+    const float2 c01 = make_float2(C.x, C.y), c23 = make_float2(C.z, C.w);
+    float2 lf01[4], rt01[4], lf23[4], rt23[4], up01[4], dn01[4], up23[4], dn23[4];
+    lf01[0] = make_float2(Lf.w, C.x);  rt01[0] = make_float2(C.y, C.z);
+    lf01[1] = make_float2(Lf.z, Lf.w); rt01[1] = make_float2(C.z, C.w);
+    lf01[2] = make_float2(Lf.y, Lf.z); rt01[2] = make_float2(C.w, Rf.x);
+    lf01[3] = make_float2(Lf.x, Lf.y); rt01[3] = make_float2(Rf.x, Rf.y);
+    lf23[0] = make_float2(C.y, C.z);   rt23[0] = make_float2(C.w, Rf.x);
+    lf23[1] = make_float2(C.x, C.y);   rt23[1] = make_float2(Rf.x, Rf.y);
+    lf23[2] = make_float2(Lf.w, C.x);  rt23[2] = make_float2(Rf.y, Rf.z);
+    lf23[3] = make_float2(Lf.z, Lf.w); rt23[3] = make_float2(Rf.z, Rf.w);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float h[8], vv[8];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        h[k] = hrow[j + k];          // offsets -4..-1
-        h[4 + k] = hrow[j + 5 + k];  // offsets +1..+4
-        vv[k] = comp(win[k], j);
-        vv[4 + k] = comp(win[5 + k], j);
-      }
-      s4[j] = lap_cell(p, hrow[4 + j], h, vv);
+    for (int k = 0; k < 4; ++k) {
+      up01[k] = make_float2(win[3 - k].x, win[3 - k].y);
+      dn01[k] = make_float2(win[5 + k].x, win[5 + k].y);
+      up23[k] = make_float2(win[3 - k].z, win[3 - k].w);
+      dn23[k] = make_float2(win[5 + k].z, win[5 + k].w);
     }
+    const float2 s01 = lap_pair(p, c01, lf01, rt01, up01, dn01);
+    const float2 s23 = lap_pair(p, c23, lf23, rt23, up23, dn23);
+    float s4[4] = {s01.x, s01.y, s23.x, s23.y};
     const uint32_t rbits = (uint32_t)(rm >> (4 * i)) & 0xFu;
     if (!ADJ) {
-      if (c.srow == i) s4[c.slane] = __fadd_rn(s4[c.slane], a.src_val);
+      if (c.srow == i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (c.slane == j) s4[j] = __fadd_rn(s4[j], a.src_val);
+      }
     } else if (MODE != WM_FORWARD && rbits) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -327,18 +381,24 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
     float *np_ = c.nrow + i * PX;
     const float4 AP = ld4(np_);
     float4 an;
+    const float2 sa = make_float2(s4[0], s4[1]), sb = make_float2(s4[2], s4[3]);
+    const float2 wa = make_float2(Wv.x, Wv.y), wb2 = make_float2(Wv.z, Wv.w);
+    const float2 pa = make_float2(AP.x, AP.y), pb = make_float2(AP.z, AP.w);
+    float2 na, nb;
     if (c.xin && gzr == 1.f) {
       // outside the sponge g = 1: the general update reduces exactly to this
-      an.x = __fsub_rn(__fmaf_rn(Wv.x, s4[0], __fadd_rn(C.x, C.x)), AP.x);
-      an.y = __fsub_rn(__fmaf_rn(Wv.y, s4[1], __fadd_rn(C.y, C.y)), AP.y);
-      an.z = __fsub_rn(__fmaf_rn(Wv.z, s4[2], __fadd_rn(C.z, C.z)), AP.z);
-      an.w = __fsub_rn(__fmaf_rn(Wv.w, s4[3], __fadd_rn(C.w, C.w)), AP.w);
+      na = sub2(fma2(wa, sa, add2(c01, c01)), pa);
+      nb = sub2(fma2(wb2, sb, add2(c23, c23)), pb);
     } else {
-      an.x = update_cell(__fmul_rn(gzr, c.gx4.x), Wv.x, s4[0], C.x, AP.x);
-      an.y = update_cell(__fmul_rn(gzr, c.gx4.y), Wv.y, s4[1], C.y, AP.y);
-      an.z = update_cell(__fmul_rn(gzr, c.gx4.z), Wv.z, s4[2], C.z, AP.z);
-      an.w = update_cell(__fmul_rn(gzr, c.gx4.w), Wv.w, s4[3], C.w, AP.w);
+      // g [2u + w s - g ap], as update_cell
+      const float2 ga = mul2(make_float2(gzr, gzr), make_float2(c.gx4.x, c.gx4.y));
+      const float2 gb = mul2(make_float2(gzr, gzr), make_float2(c.gx4.z, c.gx4.w));
+      const float2 ta = fma2(wa, sa, add2(c01, c01));
+      const float2 tb = fma2(wb2, sb, add2(c23, c23));
+      na = mul2(ga, fma2(make_float2(-ga.x, -ga.y), pa, ta));
+      nb = mul2(gb, fma2(make_float2(-gb.x, -gb.y), pb, tb));
     }
+    an = make_float4(na.x, na.y, nb.x, nb.y);
     if (c.valid) st4(np_, an);
     if (SNAP) {
       const float4 sv = make_float4(s4[0], s4[1], s4[2], s4[3]);
@@ -361,11 +421,14 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
         const float inv = dinv[i];
         float *gp = c.grow + i * W4;
         float4 gm = ld4(gp);
-        gm.x = __fmaf_rn(an.x, Snap<DT>::scaled ? dv.x * inv : dv.x, gm.x);
-        gm.y = __fmaf_rn(an.y, Snap<DT>::scaled ? dv.y * inv : dv.y, gm.y);
-        gm.z = __fmaf_rn(an.z, Snap<DT>::scaled ? dv.z * inv : dv.z, gm.z);
-        gm.w = __fmaf_rn(an.w, Snap<DT>::scaled ? dv.w * inv : dv.w, gm.w);
-        st4(gp, gm);
+        float2 da = make_float2(dv.x, dv.y), db = make_float2(dv.z, dv.w);
+        if (Snap<DT>::scaled) {
+          da = mul2(da, make_float2(inv, inv));
+          db = mul2(db, make_float2(inv, inv));
+        }
+        const float2 ga2 = fma2(na, da, make_float2(gm.x, gm.y));
+        const float2 gb2 = fma2(nb, db, make_float2(gm.z, gm.w));
+        st4(gp, make_float4(ga2.x, ga2.y, gb2.x, gb2.y));
       }
     }
     if (!ADJ && a.record && rbits) {
