@@ -325,6 +325,21 @@ def run_reference(args, cfg, P, ws_, rank):
     print(json.dumps(line))
 
 
+def reduce_over_ranks(t_ms, e2e_ms, device):
+    """Slowest rank's step time and end-to-end time (max over ranks). Every
+    rank runs an independent replica; no data crosses ranks."""
+    import torch
+    t = torch.tensor([t_ms, e2e_ms or 0.0], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t[0]), (float(t[1]) or None)
+
+
+def job_value(particles_per_rank, world, t_max_ms):
+    """Whole-job particle-gradients/s: all ranks' particles over the slowest
+    rank's step time."""
+    return particles_per_rank * world / (t_max_ms * 1e-3)
+
+
 def main():
     args = parse()
     ws_, rank, local = dist_env()
@@ -343,14 +358,12 @@ def main():
     t_max = res["t_step_ms"]
     e2e_max = res.get("e2e_ms")
     if ws_ > 1:
-        t = torch.tensor([t_max, e2e_max or 0.0], dtype=torch.float64, device="cuda:%d" % local)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_max = float(t[0]), float(t[1]) or None
+        t_max, e2e_max = reduce_over_ranks(t_max, e2e_max, "cuda:%d" % local)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
     units = P * ws_
-    value = units / (t_max * 1e-3)
+    value = job_value(P, ws_, t_max)
     cu = cell_updates_per_particle(cfg)
     peaks = {}
     try:
@@ -386,7 +399,7 @@ def main():
         "clocks": res["clocks"],
     }
     if e2e_max:
-        line["e2e"] = {"value": units / (e2e_max * 1e-3), "unit": UNIT,
+        line["e2e"] = {"value": job_value(P, ws_, e2e_max), "unit": UNIT,
                        "h2d_bytes_per_step": res["h2d_bytes"],
                        "d2h_bytes_per_step": res["d2h_bytes"]}
     if not args.no_cpu_baseline:

@@ -1,0 +1,45 @@
+"""Multi-rank logic of bench.py on CPU: two gloo ranks (world size 2) agree on
+the slowest rank's time, and the job value counts every rank's particles.
+Each rank of the benchmark runs an independent replica; the only collective
+is this timing reduction."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t, e = bench.reduce_over_ranks(100.0 + 50.0 * rank, 200.0 - 10.0 * rank, "cpu")
+    out[rank] = (t, e, bench.job_value(600, world, t))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_to_the_slowest_rank():
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn", join=True)
+    for rank in range(world):
+        t, e, v = out[rank]
+        assert t == 150.0 and e == 200.0
+        assert v == pytest.approx(1200 / 0.150)
