@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time steps (profiling cases only)")
+    ap.add_argument("--workload", default="svgd", choices=["svgd", "ssvgd", "advi"],
+                    help="svgd: the batched SVGD step (default); ssvgd / advi: the "
+                         "240x600, 40-source shape with the stochastic-SVGD or "
+                         "mean-field ADVI update")
     return ap.parse_args()
 
 
@@ -325,6 +329,88 @@ def run_reference(args, cfg, P, ws_, rank):
     print(json.dumps(line))
 
 
+def run_other_workload(args, torch):
+    """sSVGD or ADVI at the 240 x 600 / 40-source / 3000-step shape. One step:
+    ssvgd - fwi_gradient for P particles (default 40, a slice of the
+            2000-particle ensemble) and ssvgd_step on all 2000 particles
+            (d = 144,000, Cholesky of the 2000 x 2000 kernel, Philox noise);
+    advi  - 64 Philox draws, advi_sample, fwi_gradient of the 64 samples,
+            advi_step (Adam)."""
+    import paper_2310_13325_gb300 as vg
+    from paper_2310_13325_gb300 import build as vbuild
+    vbuild.build()
+    cfg = synth.config("cfg5")
+    if args.nt:
+        cfg = cfg.with_(nt=args.nt)
+    dev = torch.device("cuda:0")
+    P = args.particles or (40 if args.workload == "ssvgd" else 64)
+    geo, fwi, X0, dobs_h, sigma, lo, hi = build_problem(cfg, max(P, 2000) if args.workload == "ssvgd" else P, 0, dev, vg, torch)
+    fwi.set_autotune(not args.no_autotune)
+    dobs = torch.tensor(dobs_h, device=dev)
+    lo_t = torch.tensor(lo.reshape(-1), dtype=torch.float32, device=dev)
+    hi_t = torch.tensor(hi.reshape(-1), dtype=torch.float32, device=dev)
+    ev = []
+    if args.workload == "ssvgd":
+        n = X0.shape[0]
+        X = torch.tensor(X0, device=dev)
+        G = torch.zeros_like(X)
+        ws = torch.empty(vg.svgd_workspace_size(n, cfg.d, vg.VIP_GRAM_BF16X3, True),
+                         dtype=torch.uint8, device=dev)
+        it = [0]
+
+        def step(rec=None):
+            sl = X[:P]
+            _, g = fwi.gradient(sl, dobs, sigma)
+            G[:P].copy_(g.reshape(P, -1))
+            if rec: rec[1].record()
+            it[0] += 1
+            vg.ssvgd_step(X, G, 1e-3, seed=3, it=it[0], lo=lo_t, hi=hi_t, ws=ws, gscale=-1.0)
+    else:
+        d = cfg.d
+        mu = torch.tensor(((lo + hi) / 2).reshape(-1), dtype=torch.float32, device=dev)
+        a_t, b_t = lo_t - 1.0, hi_t + 1.0
+        mu = torch.log((mu - a_t) / (b_t - mu))
+        om = torch.full((d,), -3.0, device=dev)
+        st = torch.zeros((4, d), device=dev)
+        it = [0]
+
+        def step(rec=None):
+            it[0] += 1
+            eta = vg.philox_normal(P, d, seed=5, it=it[0], device=dev)
+            m = vg.advi_sample(mu, om, eta, a_t, b_t)
+            _, g = fwi.gradient(m, dobs, sigma)
+            if rec: rec[1].record()
+            vg.advi_step(mu, om, st, it[0], eta, g.reshape(P, -1), 0.01, a_t, b_t, gscale=-1.0)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        step(e)
+        e[2].record()
+        ev.append(e)
+    torch.cuda.synchronize()
+    t_step = float(np.mean([a.elapsed_time(c) for a, b, c in ev]))
+    t_fwi = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
+    t_upd = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
+    cu = cell_updates_per_particle(cfg)
+    line = {"metric": "FWI particle-gradients/s (%s step, 240x600 shape)" % args.workload,
+            "value": P / (t_fwi * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%s 240x600 grid dx 10 m, 40 src, 400 rec, %d steps dt 0.8 ms, "
+                                   "%d gradients per step" % (args.workload, cfg.nt, P),
+                       "plan": fwi.query_plan(P)},
+            "gcell_updates_per_s": cu * P / (t_fwi * 1e-3) / 1e9,
+            "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
+            "update": ("ssvgd_step n=2000 d=144000" if args.workload == "ssvgd"
+                       else "advi_step S=64 d=144000")}
+    if args.workload == "ssvgd":
+        line["iteration_s_for_2000_particles"] = (2000.0 / P) * t_fwi * 1e-3 + t_upd * 1e-3
+    print(json.dumps(line))
+
+
 def reduce_over_ranks(t_ms, e2e_ms, device):
     """Slowest rank's step time and end-to-end time (max over ranks). Every
     rank runs an independent replica; no data crosses ranks."""
@@ -351,6 +437,9 @@ def main():
         run_reference(args, cfg, P, ws_, rank)
         return
     import torch
+    if args.workload != "svgd":
+        run_other_workload(args, torch)
+        return
     if ws_ > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")

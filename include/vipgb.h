@@ -272,9 +272,10 @@ int  advi_sample(const float *mu, const float *omega, const float *eta,
  *   grad_mu = mean_s g_s, grad_omega = mean_s g_s eta_s e^omega + 1.
  *   adam_state [4][d]: first and second moments of mu, then of omega,
  *              zero before the first step; t >= 1 the step number.
- *   gm [S][d] d log p / dm at m_s = advi_sample(...). */
+ *   gm [S][d] gradient at m_s = advi_sample(...), with d log p / dm =
+ *      gscale * gm (1 for log-density gradients, -1 for misfit gradients). */
 int  advi_step(float *mu, float *omega, float *adam_state, int t,
-               const float *eta, const float *gm, int S, int d,
+               const float *eta, const float *gm, float gscale, int S, int d,
                const float *a, const float *b, float lr,
                vip_stream_t stream);
 

@@ -305,15 +305,16 @@ def advi_sample(mu, omega, eta, a=None, b=None, out=None, stream=None):
     return out
 
 
-def advi_step(mu, omega, adam_state, t, eta, gm, lr, a=None, b=None, stream=None):
-    """In-place Adam ascent of (mu, omega); adam_state [4, d] zero-initialised."""
+def advi_step(mu, omega, adam_state, t, eta, gm, lr, a=None, b=None, gscale=1.0, stream=None):
+    """In-place Adam ascent of (mu, omega); adam_state [4, d] zero-initialised;
+    d log p / dm = gscale * gm."""
     torch = _torch()
     S, d = eta.shape
     check(_lib.load().advi_step(_ptr(mu, torch.float32, "mu"),
                                 _ptr(omega, torch.float32, "omega"),
                                 _ptr(adam_state, torch.float32, "adam_state"), int(t),
                                 _ptr(eta, torch.float32, "eta"), _ptr(gm, torch.float32, "gm"),
-                                S, d, _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                float(gscale), S, d, _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
                                 float(lr), _stream(stream)), "advi_step")
 
 

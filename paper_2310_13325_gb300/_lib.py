@@ -52,8 +52,8 @@ _SIGS = {
                            c_uint64, c_void_p, c_void_p, c_void_p]),
     "advi_sample": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
                             c_void_p, c_void_p, c_void_p]),
-    "advi_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int,
-                          c_int, c_void_p, c_void_p, c_float, c_void_p]),
+    "advi_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_float,
+                          c_int, c_int, c_void_p, c_void_p, c_float, c_void_p]),
     "vip_philox_normal": (c_int, [c_void_p, c_int, c_int, c_uint64, c_uint64, c_void_p]),
 }
 

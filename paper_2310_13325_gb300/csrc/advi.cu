@@ -24,8 +24,8 @@ __global__ void advi_sample_kernel(const float *mu, const float *om, const float
 }
 
 __global__ void advi_step_kernel(float *mu, float *om, float *st, int t, const float *eta,
-                                 const float *gm, int S, int d, const float *a, const float *b,
-                                 float lr) {
+                                 const float *gm, float gscale, int S, int d, const float *a,
+                                 const float *b, float lr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d) return;
   const float mi = mu[i], si = expf(om[i]);
@@ -33,7 +33,7 @@ __global__ void advi_step_kernel(float *mu, float *om, float *st, int t, const f
   double gmu = 0.0, gom = 0.0;
   for (int s = 0; s < S; ++s) {
     const float e = eta[(size_t)s * d + i];
-    float g = gm[(size_t)s * d + i];
+    float g = gscale * gm[(size_t)s * d + i];
     if (a) {
       const float th = fmaf(si, e, mi);
       const float sg = 1.f / (1.f + expf(-th));
@@ -72,13 +72,13 @@ int advi_sample(const float *mu, const float *omega, const float *eta, int S, in
 }
 
 int advi_step(float *mu, float *omega, float *adam_state, int t, const float *eta,
-              const float *gm, int S, int d, const float *a, const float *b, float lr,
-              vip_stream_t stream) {
+              const float *gm, float gscale, int S, int d, const float *a, const float *b,
+              float lr, vip_stream_t stream) {
   if (!mu || !omega || !adam_state || !eta || !gm || S < 1 || d < 1 || t < 1 ||
       (!a) != (!b))
     return VIP_ERR_ARG;
-  advi_step_kernel<<<idiv_up(d, 256), 256, 0, stream>>>(mu, omega, adam_state, t, eta, gm, S, d,
-                                                        a, b, lr);
+  advi_step_kernel<<<idiv_up(d, 256), 256, 0, stream>>>(mu, omega, adam_state, t, eta, gm, gscale,
+                                                        S, d, a, b, lr);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }

@@ -50,4 +50,4 @@ def test_strerror_and_argument_checks(lib):
     assert lib.svgd_workspace_size(600, 36000, 1, 1) > 600 * 36000 * 4
     # null arguments
     assert lib.svgd_step(None, None, 1.0, 4, 4, 0.1, 0.0, None, None, 1, None, 0, None, None) == -1
-    assert lib.advi_step(None, None, None, 1, None, None, 1, 1, None, None, 0.1, None) == -1
+    assert lib.advi_step(None, None, None, 1, None, None, 1.0, 1, 1, None, None, 0.1, None) == -1

@@ -224,3 +224,36 @@ def test_full_size_cfg3_sampled_traces_and_gradient_direction():
     fd = (Jp.item() - Jm.item()) / (2 * h)
     an = float((G0.reshape(-1).double() * dv.reshape(-1).double()).sum())
     assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)
+
+
+def test_largest_grid_sampled_traces_and_gradient_direction():
+    """240 x 600 grid (280 x 640 padded), 3000 steps at 0.8 ms: the largest
+    workload's geometry needs clusters beyond the portable size of 8 CTAs.
+    Two sources, one particle: traces against the oracle, the linearisation
+    dot product, and the plan for 2000 particles fits memory."""
+    cfg = synth.config("cfg5").with_(nsrc=2)
+    geo = synth.geometry(cfg)
+    g = ofwi.Geom.from_config(cfg, geo)
+    v_true = synth.true_model(cfg)
+    lo, hi = synth.prior_bounds(cfg, v_true)
+    V = synth.particles_from_prior(lo, hi, 1, seed=2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    seis = fwi.forward(_t(V))
+    ref = ofwi.forward(V[0].reshape(cfg.nz, cfg.nx), g, 1)
+    assert rel(seis[0, 1].cpu().numpy(), ref) <= 1e-5
+    # linearisation dot product <J dv, r> = <dv, J^T r>: central difference of
+    # the traces with h = 5 m/s along dv ~ N(0, 5^2) (FP32 trace noise is then
+    # below 1e-3 of the difference, the O(h^2) term below 1e-4)
+    gen = torch.Generator(device=DEV).manual_seed(5)
+    v0 = _t(V).reshape(1, cfg.nz, cfg.nx)
+    dv = torch.randn(v0.shape, generator=gen, device=DEV) * 5.0
+    r = torch.randn((1, g.nsrc, g.nrec, g.nt), generator=gen, device=DEV)
+    h = 5.0
+    Jdv = (fwi.forward(v0 + h * dv) - fwi.forward(v0 - h * dv)).double() / (2 * h)
+    lhs = float((Jdv * r.double()).sum())
+    rhs = float((fwi.adjoint(v0, r).double() * dv.double()).sum())
+    assert abs(lhs - rhs) <= 2e-3 * abs(rhs), (lhs, rhs)
+    full = vg.Fwi.from_config(synth.config("cfg5"), synth.geometry(synth.config("cfg5")))
+    plan = full.query_plan(2000)
+    print("largest workload plan:", plan)
+    assert plan["cluster_ctas"] >= 1 and plan["concurrent_pairs"] >= 1
