@@ -49,7 +49,7 @@ struct Tables {
   int Q, V, Hb, NXg, ntask_pad;
   float *gz = nullptr, *gx = nullptr;
   unsigned long long *rmask = nullptr;
-  int *rbase = nullptr, *rperm = nullptr, *rbstart = nullptr;
+  int *rbase = nullptr, *rperm = nullptr, *rbstart = nullptr, *roff = nullptr;
   int rmax = 0;   // largest number of receivers in one band
 };
 
@@ -106,9 +106,14 @@ static int band_height(int NZ, int Q, int V) {
 
 static int receiver_pad(int R) { return (R + 3) & ~3; }
 
-static size_t wave_smem(int Hb, int PX, int NXg, bool grad, int R) {
-  size_t f = 2 * (size_t)Hb * PX + PX + (grad ? 2 : 1) * (size_t)Hb * NXg * 4 +
-             ((Hb + 3) & ~3) + (size_t)NXg * 4 + 3 * (size_t)receiver_pad(R);
+// Shared memory of the batched kernel (floats): two levels, the zero row, w'
+// and (gradient) the accumulator, all [Hb][PX]; (gz, gz) per row; the
+// column taper; one flag per strip; receiver numbers, cell offsets and two
+// value slots.
+static size_t wave_smem(int Hb, int V, int PX, int NXg, bool grad, int R) {
+  const size_t HP = (size_t)Hb * PX;
+  size_t f = (grad ? 4 : 3) * HP + PX + ((2 * Hb + 3) & ~3) + (size_t)NXg * 4 +
+             ((Hb / V + 3) & ~3) + 4 * (size_t)receiver_pad(R);
   return f * 4;
 }
 
@@ -140,19 +145,26 @@ static int get_tables(fwi_ctx *c, int Q, int V, Tables **out) {
     order[r] = {((long)b * t.ntask_pad + task) * 64 + bit, r};
   }
   std::sort(order.begin(), order.end());
+  // cell offset of each receiver in its band's level buffer (row pitch PX,
+  // cells from column 4)
+  const int PX = 4 * (t.NXg + 2);
+  std::vector<int> roff(std::max(c->R, 1), 0);
   for (int i = 0; i < c->R; ++i) {
     const long key = order[i][0];
     const long bt = key / 64;
     const int bit = (int)(key % 64);
     if (mask[bt] == 0) base[bt] = i;
     mask[bt] |= 1ull << bit;
-    perm[i] = (int)order[i][1];
+    const int r = (int)order[i][1];
+    perm[i] = r;
+    roff[i] = (c->rec_z[r] % t.Hb) * PX + 4 + c->rec_x[r];
   }
   VIP_TRY(cudaMalloc(&t.gz, gz.size() * 4));
   VIP_TRY(cudaMalloc(&t.gx, gx.size() * 4));
   VIP_TRY(cudaMalloc(&t.rmask, mask.size() * 8));
   VIP_TRY(cudaMalloc(&t.rbase, base.size() * 4));
   VIP_TRY(cudaMalloc(&t.rperm, perm.size() * 4));
+  VIP_TRY(cudaMalloc(&t.roff, roff.size() * 4));
   std::vector<int> bstart(Q + 1, 0);
   for (int i = 0; i < c->R; ++i) bstart[order[i][0] / 64 / t.ntask_pad + 1]++;
   for (int b = 0; b < Q; ++b) {
@@ -166,6 +178,7 @@ static int get_tables(fwi_ctx *c, int Q, int V, Tables **out) {
   VIP_TRY(cudaMemcpy(t.rmask, mask.data(), mask.size() * 8, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(t.rbase, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(t.rperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
+  VIP_TRY(cudaMemcpy(t.roff, roff.data(), roff.size() * 4, cudaMemcpyHostToDevice));
   c->tables.push_back(t);
   *out = &c->tables.back();
   return VIP_OK;
@@ -222,7 +235,7 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
       if (Hb < 4) continue;
       const int NXg = idiv_up(c->NX, 4);
       const int PX = 4 * (NXg + 2);
-      const size_t smem = wave_smem(Hb, PX, NXg, grad, c->R);
+      const size_t smem = wave_smem(Hb, V, PX, NXg, grad, c->R);
       if (smem + fa.sharedSizeBytes > c->smem_optin) continue;
       const int ntask = (Hb / V) * NXg;
       const int ntask_pad = idiv_up(ntask, 32) * 32;
@@ -384,7 +397,7 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   wp.gz = tb->gz; wp.gx = tb->gx; wp.wavelet = c->d_wavelet;
   wp.src_z = c->d_src_z; wp.src_x = c->d_src_x;
   wp.rmask = tb->rmask; wp.rbase = tb->rbase; wp.rperm = tb->rperm;
-  wp.rbstart = tb->rbstart; wp.Rpad = receiver_pad(c->R);
+  wp.rbstart = tb->rbstart; wp.roff = tb->roff; wp.Rpad = receiver_pad(c->R);
   wp.items = pl.items; wp.ipp = pl.ipp; wp.spi = pl.spi;
   wp.K = pl.K; wp.nseg = pl.nseg;
   wp.status = c->d_status;
@@ -865,7 +878,7 @@ void fwi_destroy(fwi_ctx *c) {
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto &t : c->tables) {
     cudaFree(t.gz); cudaFree(t.gx); cudaFree(t.rmask); cudaFree(t.rbase); cudaFree(t.rperm);
-    cudaFree(t.rbstart);
+    cudaFree(t.rbstart); cudaFree(t.roff);
   }
   cudaFree(c->scratch);
   cudaFree(c->d_wavelet); cudaFree(c->d_src_z); cudaFree(c->d_src_x); cudaFree(c->d_status);

@@ -67,6 +67,7 @@ struct WaveParams {
   const int *rbase;      // [Q*ntask_pad] first entry in rperm
   const int *rperm;      // [R] receiver numbers in task order
   const int *rbstart;    // [Q+1] first rperm entry of each band
+  const int *roff;       // [R] cell offset of each rperm entry within its band's level buffer
   int Rpad;              // receiver slots per band in shared memory
   // work decomposition
   int P, items, ipp, spi;
@@ -208,34 +209,41 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 
 // Laplacian bracket of the cell pair (j, j+1): lf[k], rt[k] the neighbours at
-// distance k+1 to the left and right, up[k], dn[k] above and below; same
-// operation order per lane as lap_cell.
-__device__ __forceinline__ float2 lap_pair(const WaveParams &p, float2 u, const float2 lf[4],
-                                           const float2 rt[4], const float2 up[4],
-                                           const float2 dn[4]) {
+// distance k+1 to the left and right, up[k], dn[k] above and below, kN the
+// coefficient c_N in both lanes; same operation order per lane as lap_cell.
+__device__ __forceinline__ float2 lap_pair(float2 k1, float2 k2, float2 k3, float2 k4, float2 u,
+                                           const float2 lf[4], const float2 rt[4],
+                                           const float2 up[4], const float2 dn[4]) {
   const float2 u4 = mul2(make_float2(4.f, 4.f), u);
-  float2 s = mul2(make_float2(p.c4, p.c4),
-                  sub2(add2(add2(lf[3], rt[3]), add2(up[3], dn[3])), u4));
-  s = fma2(make_float2(p.c3, p.c3), sub2(add2(add2(lf[2], rt[2]), add2(up[2], dn[2])), u4), s);
-  s = fma2(make_float2(p.c2, p.c2), sub2(add2(add2(lf[1], rt[1]), add2(up[1], dn[1])), u4), s);
-  s = fma2(make_float2(p.c1, p.c1), sub2(add2(add2(lf[0], rt[0]), add2(up[0], dn[0])), u4), s);
+  float2 s = mul2(k4, sub2(add2(add2(lf[3], rt[3]), add2(up[3], dn[3])), u4));
+  s = fma2(k3, sub2(add2(add2(lf[2], rt[2]), add2(up[2], dn[2])), u4), s);
+  s = fma2(k2, sub2(add2(add2(lf[1], rt[1]), add2(up[1], dn[1])), u4), s);
+  s = fma2(k1, sub2(add2(add2(lf[0], rt[0]), add2(up[0], dn[0])), u4), s);
   return s;
 }
 
 // ---------------------------------------------------------------------------
 // Batched persistent cluster kernel.
+//
+// Shared memory of a CTA (floats): the two time levels U[0], U[1] and the
+// arrays W (w') and Gm (gradient accumulator) all use the row pitch PX, with
+// the cells of a row at columns 4 .. 4+NXg*4-1, so one cell has the same
+// offset in all four; a row of zeros; the row taper as (gz, gz) pairs; the
+// column taper; one flag per strip (taper 1 on all its rows); the band's
+// receiver numbers, cell offsets and two steps of receiver values.
 struct Band {
   float *U[2];                 // local field buffers [Hb][PX]
-  uint32_t su[2];              // their shared-window addresses
   uint32_t sup[2], sdn[2];     // neighbours' buffers in the cluster window
   bool has_up, has_dn;         // whether the band has a neighbour above / below
   uint32_t szr;                // address of one row of zeros
-  float *W;                    // [Hb][NXg*4] w'
-  float *Gm;                   // [Hb][NXg*4] gradient accumulator
-  float *gzs;                  // [Hb]
+  float *W;                    // [Hb][PX] w'
+  float *Gm;                   // [Hb][PX] gradient accumulator
+  float2 *gz2;                 // [Hb] (gz, gz) per row
   float *gxs;                  // [NXg*4]
+  int *sfast;                  // [nstrip] 1 when the taper is 1 on every row of the strip
   int *rid;                    // [Rpad] receiver numbers of this band (rperm order)
-  float *val;                  // [2][Rpad] per-receiver values of the next two steps
+  int *roff;                   // [Rpad] their cell offsets in a level buffer
+  float *val;                  // [2][Rpad] per-receiver values of two consecutive steps
   int rb0, nrb;                // first rperm entry and number of receivers of the band
   int b;
 };
@@ -260,6 +268,23 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
+// Split cluster barrier. A time step ends with step_fence(): the arrive
+// publishes the step's shared-memory writes to the cluster, the CTA barrier
+// makes them visible inside the CTA. The matching wait comes inside the next
+// band_step, just before the first strip that reads a neighbouring band or
+// overwrites rows a neighbour reads; the strips in between overlap the
+// cluster barrier. A run of steps is closed with cluster_wait().
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void step_fence() {
+  cluster_arrive();
+  __syncthreads();
+}
+
 // Per-step context of the cell loop.
 struct StepArgs {
   int ph;            // which local buffer holds the current level
@@ -269,11 +294,12 @@ struct StepArgs {
   int s;             // source number
   int src_task, src_bit;   // forward source position in this CTA (or -1)
   float src_val;
-  bool record;       // forward: write traces / residuals
+  bool record;       // forward: record the current level at the receivers
   size_t dofs;       // element offset of this step's snapshot slab
   size_t sofs;       // offset of this step's scale slab
   long long dnext;   // adjoint: element offset of the next step's slab (-1: none)
-  int vnext_t;       // trace sample whose receiver values the next step uses (-1: none)
+  int vnext_t;       // sample whose receiver values are fetched in this step (-1: none)
+  int vnext_par;     // value slot they go to
   double *Jacc;      // per-thread squared-residual accumulator
 };
 
@@ -283,28 +309,40 @@ template <> struct MaskT<10> { using type = unsigned long long; };
 
 // Per-task constants of one step.
 struct TaskCtx {
-  const float *crow;   // current level, row r0, column group (shared)
-  float *nrow;         // next level, row r0
-  const float *wrow;   // w', row r0
-  float *grow;         // accumulator, row r0
-  const float *gz;     // taper, row r0
-  float4 gx4;
-  bool xin;            // all four columns outside the sponge
+  const float *cur;    // current level at (row r0, first cell of the task), own CTA
+  const float2 *gz;    // (gz, gz) of row r0
+  uint32_t top, tstr;  // cluster-window address of row r0-4 and row stride above the task
+  uint32_t bot, bstr;  // same for row r0+V below the task
+  bool tedge, bedge;   // rows above / below come from a neighbour or the zero row
+  float2 gxa, gxb;     // column taper of the cell pairs (0,1) and (2,3)
+  bool fast;           // taper 1 on every cell of the task
+  bool special;        // forward: holds the source; adjoint: holds receivers
   bool valid;
   int srow, slane;     // source row within the task (-1: none) and lane
   int rb;              // band-local index of the task's first receiver
-  int r0, gcol;
 };
 
+// Add v to lane j of the cell quadruple held as the pairs (s01, s23).
+__device__ __forceinline__ void add_lane(float2 &s01, float2 &s23, int j, float v) {
+  if (j == 0) s01.x = __fadd_rn(s01.x, v);
+  else if (j == 1) s01.y = __fadd_rn(s01.y, v);
+  else if (j == 2) s23.x = __fadd_rn(s23.x, v);
+  else s23.y = __fadd_rn(s23.y, v);
+}
+
+// The V rows of one task, 4 adjacent cells per row, top to bottom. Offsets
+// (floats) from c.cur: dn to the next level, dW to w', dG to the gradient
+// accumulator; PX is the row pitch of all four. The vertical stencil window
+// of 9 rows lives in registers; each row loads one new window row, its left
+// and right neighbour quadruples, w' and the previous value.
 template <int V, bool ADJ, bool SNAP, int MODE, class DT>
-__device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, const StepArgs &a,
-                                          const TaskCtx &c, typename MaskT<V>::type rm,
-                                          DT *Dtask, const DT *Dnext, const float *Stask,
-                                          float *Sw, const float *vcur, uint32_t up_s,
-                                          uint32_t dn_s, uint32_t cur_s, bool edge, int tid) {
+__device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
+                                          typename MaskT<V>::type rm, DT *Dtask,
+                                          const DT *Dnext, const float *Stask, float *Sw,
+                                          const float *vcur, int PX, int dn, int dW, int dG,
+                                          int W4, float2 k1, float2 k2, float2 k3, float2 k4,
+                                          int tid) {
   using M = typename MaskT<V>::type;
-  const int PX = p.PX, W4 = p.NXg * 4, Hb = p.Hb;
-  const uint32_t rowb = (uint32_t)PX * 4u;
   // adjoint: snapshot rows are loaded two rows ahead of their use
   float4 dq[V];
   float dinv[V];
@@ -315,29 +353,26 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
       dq[i] = Snap<DT>::ld(Dtask, (size_t)i * W4, 1.f);
     }
   }
-  // the 9-row vertical window: rows r0-4 .. r0+3 first. Strips away from
-  // the band edges read their own rows; edge strips map each row to the
-  // neighbouring band or the zero row.
-  const uint32_t colb = (uint32_t)(c.gcol + 4) * 4u;
-  const uint32_t wb = cur_s + (uint32_t)(c.r0 - 4) * rowb + colb;
-  auto wrow_addr = [&](int i) -> uint32_t {
-    if (!edge) return wb + (uint32_t)i * rowb;
-    const int rr = c.r0 - 4 + i;
-    if (rr < 0) return B.has_up ? up_s + (uint32_t)(rr + Hb) * rowb + colb : B.szr + colb;
-    if (rr >= Hb) return B.has_dn ? dn_s + (uint32_t)(rr - Hb) * rowb + colb : B.szr + colb;
-    return wb + (uint32_t)i * rowb;
-  };
+  float *cp = const_cast<float *>(c.cur);
+  // window rows r0-4 .. r0+3; the four above the task come from the
+  // neighbouring band (or the zero row) for the top strip
   float4 win[9];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) win[i] = ld_cluster4(wrow_addr(i));
+  for (int j = 0; j < 4; ++j)
+    win[j] = c.tedge ? ld_cluster4(c.top + (uint32_t)j * c.tstr) : ld4(cp + (j - 4) * PX);
+#pragma unroll
+  for (int j = 4; j < 8; ++j) win[j] = ld4(cp + (j - 4) * PX);
 #pragma unroll
   for (int i = 0; i < V; ++i) {
     if (ADJ && SNAP && i + 2 < V) {
       dinv[i + 2] = Snap<DT>::scaled ? Stask[i + 2] : 1.f;
       dq[i + 2] = Snap<DT>::ld(Dtask, (size_t)(i + 2) * W4, 1.f);
     }
-    win[8] = ld_cluster4(wrow_addr(i + 8));
-    const float *rp = c.crow + i * PX;
+    float *rp = cp + i * PX;
+    if (i + 4 < V)
+      win[8] = ld4(rp + 4 * PX);
+    else
+      win[8] = c.bedge ? ld_cluster4(c.bot + (uint32_t)(i + 4 - V) * c.bstr) : ld4(rp + 4 * PX);
     const float4 Lf = ld4(rp - 4), Rf = ld4(rp + 4), C = win[4];
     // cell pairs (0,1) and (2,3): neighbours at distance 1..4
     const float2 c01 = make_float2(C.x, C.y), c23 = make_float2(C.z, C.w);
@@ -357,52 +392,44 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
       up23[k] = make_float2(win[3 - k].z, win[3 - k].w);
       dn23[k] = make_float2(win[5 + k].z, win[5 + k].w);
     }
-    const float2 s01 = lap_pair(p, c01, lf01, rt01, up01, dn01);
-    const float2 s23 = lap_pair(p, c23, lf23, rt23, up23, dn23);
-    float s4[4] = {s01.x, s01.y, s23.x, s23.y};
-    const uint32_t rbits = (uint32_t)(rm >> (4 * i)) & 0xFu;
-    if (!ADJ) {
-      if (c.srow == i) {
+    float2 s01 = lap_pair(k1, k2, k3, k4, c01, lf01, rt01, up01, dn01);
+    float2 s23 = lap_pair(k1, k2, k3, k4, c23, lf23, rt23, up23, dn23);
+    if (c.special) {
+      if (!ADJ) {
+        if (c.srow == i) add_lane(s01, s23, c.slane, a.src_val);
+      } else if (MODE != WM_FORWARD) {
+        const uint32_t rbits = (uint32_t)(rm >> (4 * i)) & 0xFu;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (c.slane == j) s4[j] = __fadd_rn(s4[j], a.src_val);
-      }
-    } else if (MODE != WM_FORWARD && rbits) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (rbits & (1u << j)) {
-          const int lr = c.rb + __popcll((unsigned long long)(rm & (((M)1 << (4 * i + j)) - 1)));
-          s4[j] = __fadd_rn(s4[j], vcur[lr]);
+        for (int j = 0; j < 4; ++j) {
+          if (rbits & (1u << j)) {
+            const int lr = c.rb + __popcll((unsigned long long)(rm & (((M)1 << (4 * i + j)) - 1)));
+            add_lane(s01, s23, j, vcur[lr]);
+          }
         }
       }
     }
-    const float4 Wv = ld4(c.wrow + i * W4);
-    const float gzr = c.gz[i];
-    float *np_ = c.nrow + i * PX;
-    const float4 AP = ld4(np_);
-    float4 an;
-    const float2 sa = make_float2(s4[0], s4[1]), sb = make_float2(s4[2], s4[3]);
-    const float2 wa = make_float2(Wv.x, Wv.y), wb2 = make_float2(Wv.z, Wv.w);
+    const float4 Wv = ld4(rp + dW);
+    const float4 AP = ld4(rp + dn);
+    const float2 wa = make_float2(Wv.x, Wv.y), wb = make_float2(Wv.z, Wv.w);
     const float2 pa = make_float2(AP.x, AP.y), pb = make_float2(AP.z, AP.w);
+    const float2 ta = fma2(wa, s01, add2(c01, c01));
+    const float2 tb = fma2(wb, s23, add2(c23, c23));
     float2 na, nb;
-    if (c.xin && gzr == 1.f) {
-      // outside the sponge g = 1: the general update reduces exactly to this
-      na = sub2(fma2(wa, sa, add2(c01, c01)), pa);
-      nb = sub2(fma2(wb2, sb, add2(c23, c23)), pb);
+    if (c.fast) {
+      // taper 1: g [t - g ap] reduces exactly to t - ap
+      na = sub2(ta, pa);
+      nb = sub2(tb, pb);
     } else {
       // g [2u + w s - g ap], as update_cell
-      const float2 ga = mul2(make_float2(gzr, gzr), make_float2(c.gx4.x, c.gx4.y));
-      const float2 gb = mul2(make_float2(gzr, gzr), make_float2(c.gx4.z, c.gx4.w));
-      const float2 ta = fma2(wa, sa, add2(c01, c01));
-      const float2 tb = fma2(wb2, sb, add2(c23, c23));
+      const float2 gz = c.gz[i];
+      const float2 ga = mul2(gz, c.gxa), gb = mul2(gz, c.gxb);
       na = mul2(ga, fma2(make_float2(-ga.x, -ga.y), pa, ta));
       nb = mul2(gb, fma2(make_float2(-gb.x, -gb.y), pb, tb));
     }
-    an = make_float4(na.x, na.y, nb.x, nb.y);
-    if (c.valid) st4(np_, an);
+    if (c.valid) st4(rp + dn, make_float4(na.x, na.y, nb.x, nb.y));
     if (SNAP) {
-      const float4 sv = make_float4(s4[0], s4[1], s4[2], s4[3]);
       if (!ADJ) {
+        const float4 sv = make_float4(s01.x, s01.y, s23.x, s23.y);
         float mul = 1.f;
         if (Snap<DT>::scaled) {
           float m = c.valid ? fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)),
@@ -419,8 +446,8 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
       } else if (c.valid) {
         const float4 dv = dq[i];
         const float inv = dinv[i];
-        float *gp = c.grow + i * W4;
-        float4 gm = ld4(gp);
+        float *gp = rp + dG;
+        const float4 gm = ld4(gp);
         float2 da = make_float2(dv.x, dv.y), db = make_float2(dv.z, dv.w);
         if (Snap<DT>::scaled) {
           da = mul2(da, make_float2(inv, inv));
@@ -429,24 +456,6 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
         const float2 ga2 = fma2(na, da, make_float2(gm.x, gm.y));
         const float2 gb2 = fma2(nb, db, make_float2(gm.z, gm.w));
         st4(gp, make_float4(ga2.x, ga2.y, gb2.x, gb2.y));
-      }
-    }
-    if (!ADJ && a.record && rbits) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (rbits & (1u << j)) {
-          const int lr = c.rb + __popcll((unsigned long long)(rm & (((M)1 << (4 * i + j)) - 1)));
-          const int rr = B.rid[lr];
-          const float d = comp(an, j);
-          if (MODE == WM_FORWARD) {
-            p.seis[((size_t)a.pair * p.R + rr) * p.N + a.t] = d;
-          } else if (MODE == WM_GRADIENT) {
-            const double res = (double)d - (double)vcur[lr];
-            *a.Jacc = __fma_rn(res, res, *a.Jacc);
-            p.rho[a.slot * p.rhoslot + (size_t)rr * p.N + a.t] =
-                (float)(res * (double)p.rho_scale);
-          }
-        }
       }
     }
 #pragma unroll
@@ -459,26 +468,53 @@ __device__ __forceinline__ void task_rows(const WaveParams &p, const Band &B, co
   }
 }
 
+// Forward sweep: the level a^t held in lev is trace sample t-1. Traces
+// (forward modelling) or residuals against the observed sample, parked in
+// value slot (t-1)&1 by the thread that reads it here (gradient). The
+// adjoint-only mode records nothing.
+template <int MODE>
+__device__ __forceinline__ void record_receivers(const WaveParams &p, const Band &B,
+                                                 const float *lev, int t, int pair, int slot,
+                                                 double *Jacc, int tid, int T) {
+  const float *vrec = B.val + ((t - 1) & 1) * p.Rpad;
+  for (int q = tid; q < B.nrb; q += T) {
+    const int rr = B.rid[q];
+    const float d = lev[B.roff[q]];
+    if (MODE == WM_FORWARD) {
+      p.seis[((size_t)pair * p.R + rr) * p.N + (t - 1)] = d;
+    } else if (MODE == WM_GRADIENT) {
+      const double res = (double)d - (double)vrec[q];
+      *Jacc = __fma_rn(res, res, *Jacc);
+      p.rho[slot * p.rhoslot + (size_t)rr * p.N + (t - 1)] = (float)(res * (double)p.rho_scale);
+    }
+  }
+}
+
 // One time step of the band: every thread updates its tasks (4 adjacent
-// cells x V rows). Window rows come from the CTA's own shared memory, or for
-// the strips at either band edge from the cluster's shared-memory window
-// (neighbouring bands, or the zero row at the grid boundary).
+// cells x V rows). Tasks are numbered so that the strips away from the band
+// edges come first: they touch no row a neighbouring band reads, so they run
+// before the wait on the previous step's cluster barrier. The strips at the
+// band edges follow the wait; their window rows beyond the band come from
+// the neighbouring bands' shared memory (or the zero row at the grid edge).
 template <int V, bool ADJ, bool SNAP, int MODE, class DT>
 __device__ __forceinline__ void band_step(const WaveParams &p, const Band &B,
                                           const StepArgs &a, int tid, int T) {
   using M = typename MaskT<V>::type;
   const int Hb = p.Hb, PX = p.PX, NXg = p.NXg, W4 = NXg * 4;
-  const float *cur = a.ph ? B.U[1] : B.U[0];
+  float *cur = a.ph ? B.U[1] : B.U[0];
   float *nxt = a.ph ? B.U[0] : B.U[1];
-  const uint32_t cur_s = a.ph ? B.su[1] : B.su[0];
+  const int dn = (int)(nxt - cur), dW = (int)(B.W - cur), dG = (int)(B.Gm - cur);
   const uint32_t up_s = a.ph ? B.sup[1] : B.sup[0];
   const uint32_t dn_s = a.ph ? B.sdn[1] : B.sdn[0];
+  const uint32_t rowb = (uint32_t)PX * 4u;
   DT *Dp = reinterpret_cast<DT *>(p.Dbuf) + a.slot * p.Dslot + a.dofs;
   const DT *Dn = a.dnext >= 0 ? reinterpret_cast<const DT *>(p.Dbuf) + a.slot * p.Dslot + a.dnext
                               : nullptr;
   float *Sp = Snap<DT>::scaled ? p.Dscale + a.slot * p.DSslot + a.sofs : nullptr;
   const float *vcur = B.val + (a.t & 1) * p.Rpad;
-  // receiver values of the next step are fetched now and parked in shared
+  if (!ADJ && a.record && a.t >= 1)
+    record_receivers<MODE>(p, B, cur, a.t, a.pair, a.slot, a.Jacc, tid, T);
+  // receiver values of a later step are fetched now and parked in shared
   // memory at the end of this step, so no dependent global load sits on the
   // critical path of the receiver rows
   float vnext[4];
@@ -499,61 +535,89 @@ __device__ __forceinline__ void band_step(const WaveParams &p, const Band &B,
       }
     }
   }
+  const float2 k1 = make_float2(p.c1, p.c1), k2 = make_float2(p.c2, p.c2);
+  const float2 k3 = make_float2(p.c3, p.c3), k4 = make_float2(p.c4, p.c4);
   const int nstrip = Hb / V;
+  const int nin = (nstrip > 2 ? nstrip - 2 : 0) * NXg;   // tasks of the inner strips
+  // the FP16 snapshot scale is a warp-wide maximum: every lane takes part
+  constexpr bool all_lanes = Snap<DT>::scaled && !ADJ && SNAP;
+  bool waited = false;
   for (int task0 = tid; task0 < p.ntask_pad; task0 += T) {
+    // warp-uniform: the warp's 32 consecutive tasks reach the edge strips
+    if (!waited && (task0 | 31) >= nin) {
+      cluster_wait();
+      waited = true;
+    }
     TaskCtx c;
     c.valid = task0 < p.ntask;
-    const int task = c.valid ? task0 : p.ntask - 1;
-    const int sp = task / NXg;
-    const int cgp = task - sp * NXg;
-    c.r0 = sp * V;
-    c.gcol = cgp * 4;
-    const int col = c.gcol + 4;
-    c.crow = cur + c.r0 * PX + col;
-    c.nrow = nxt + c.r0 * PX + col;
-    c.wrow = B.W + c.r0 * W4 + c.gcol;
-    c.grow = B.Gm + c.r0 * W4 + c.gcol;
-    c.gz = B.gzs + c.r0;
-    c.gx4 = ld4(B.gxs + c.gcol);
-    c.xin = c.gx4.x == 1.f && c.gx4.y == 1.f && c.gx4.z == 1.f && c.gx4.w == 1.f;
+    if (!all_lanes && !c.valid) break;
+    const int t = c.valid ? task0 : p.ntask - 1;
+    int sp, cgp;
+    if (t < nin) {
+      sp = 1 + t / NXg;
+      cgp = t - (sp - 1) * NXg;
+    } else {
+      const int e = t - nin;
+      sp = e < NXg ? 0 : nstrip - 1;
+      cgp = e < NXg ? e : e - NXg;
+    }
+    const int task = sp * NXg + cgp;   // row-major task number of the tables
+    const int r0 = sp * V, gcol = cgp * 4;
+    c.cur = cur + r0 * PX + gcol + 4;
+    c.gz = B.gz2 + r0;
+    const uint32_t colb = (uint32_t)(gcol + 4) * 4u;
+    c.tedge = sp == 0;
+    c.bedge = sp == nstrip - 1;
+    c.top = B.has_up ? up_s + (uint32_t)(Hb - 4) * rowb + colb : B.szr + colb;
+    c.tstr = B.has_up ? rowb : 0u;
+    c.bot = B.has_dn ? dn_s + colb : B.szr + colb;
+    c.bstr = B.has_dn ? rowb : 0u;
+    const float4 gx4 = ld4(B.gxs + gcol);
+    c.gxa = make_float2(gx4.x, gx4.y);
+    c.gxb = make_float2(gx4.z, gx4.w);
+    c.fast = B.sfast[sp] != 0 && gx4.x == 1.f && gx4.y == 1.f && gx4.z == 1.f && gx4.w == 1.f;
     M rm = 0;
     c.rb = 0;
-    if ((!ADJ && a.record) || (ADJ && MODE != WM_FORWARD)) {
+    c.srow = -1;
+    c.slane = 0;
+    c.special = false;
+    if (!ADJ) {
+      if (c.valid && task == a.src_task) {
+        c.srow = a.src_bit >> 2;
+        c.slane = a.src_bit & 3;
+        c.special = true;
+      }
+    } else if (MODE != WM_FORWARD) {
       rm = c.valid ? (M)__ldg(&p.rmask[B.b * p.ntask_pad + task]) : (M)0;
-      c.rb = __ldg(&p.rbase[B.b * p.ntask_pad + task]) - B.rb0;   // band-local
+      c.special = rm != 0;
+      if (c.special) c.rb = __ldg(&p.rbase[B.b * p.ntask_pad + task]) - B.rb0;   // band-local
     }
-    c.srow = (!ADJ && c.valid && task == a.src_task) ? (a.src_bit >> 2) : -1;
-    c.slane = a.src_bit & 3;
-    const size_t toff = (size_t)c.r0 * W4 + c.gcol;
+    const size_t toff = (size_t)r0 * W4 + gcol;
     DT *Dt = Dp + toff;
     const DT *Dnt = Dn ? Dn + toff : nullptr;
     const float *St = Sp ? Sp + (task0 / 32) * V : nullptr;
     float *Sw = Sp ? Sp + (task0 / 32) * V : nullptr;
-    const bool edge = (sp == 0) || (sp == nstrip - 1);
-    task_rows<V, ADJ, SNAP, MODE, DT>(p, B, a, c, rm, Dt, Dnt, St, Sw, vcur, up_s, dn_s, cur_s,
-                                      edge, tid);
+    task_rows<V, ADJ, SNAP, MODE, DT>(a, c, rm, Dt, Dnt, St, Sw, vcur, PX, dn, dW, dG, W4, k1,
+                                      k2, k3, k4, tid);
   }
-  // forward step n feeds step n+1, adjoint step k feeds step k-1: both have
-  // the parity of t+1
+  if (!waited) cluster_wait();
   if (fetch) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (tid + u * T < B.nrb) B.val[((a.t + 1) & 1) * p.Rpad + tid + u * T] = vnext[u];
+      if (tid + u * T < B.nrb) B.val[a.vnext_par * p.Rpad + tid + u * T] = vnext[u];
   }
 }
 
-// Value used at the receivers in the first step of a sweep (before the
-// per-step prefetch takes over): dobs at sample t (forward) or the adjoint
-// source at sample t (adjoint), into slot `par`.
-template <bool ADJ, int MODE>
+// Value used at the receivers in the first step of an adjoint sweep (before
+// the per-step fetch takes over): the adjoint source at sample t, into slot
+// par.
+template <int MODE>
 __device__ __forceinline__ void receiver_values(const WaveParams &p, const Band &B, int tid,
-                                                int slot, int s, int pair, int t, int par) {
+                                                int slot, int pair, int t, int par) {
   for (int q = tid; q < B.nrb; q += blockDim.x) {
     const int rr = B.rid[q];
     float v;
-    if (!ADJ)
-      v = p.dobs[((size_t)s * p.R + rr) * p.N + t];
-    else if (MODE == WM_GRADIENT)
+    if (MODE == WM_GRADIENT)
       v = p.rho[slot * p.rhoslot + (size_t)rr * p.N + t];
     else
       v = __fmul_rn(p.rho_scale, p.dseis[((size_t)pair * p.R + rr) * p.N + t]);
@@ -597,34 +661,48 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
   const int tid = threadIdx.x, T = blockDim.x;
   extern __shared__ __align__(16) float smem[];
   const int HP = p.Hb * p.PX;
-  const int HW = p.Hb * p.NXg * 4;
+  const int W4 = p.NXg * 4;
+  const int HW = p.Hb * W4;
+  const int nstrip = p.Hb / V;
   Band B;
   B.b = b;
   B.U[0] = smem;
   B.U[1] = smem + HP;
   float *Zr = smem + 2 * HP;
   B.W = Zr + p.PX;
-  B.Gm = B.W + HW;
-  B.gzs = B.Gm + (MODE != WM_FORWARD ? HW : 0);
-  B.gxs = B.gzs + ((p.Hb + 3) & ~3);
-  B.rid = reinterpret_cast<int *>(B.gxs + p.NXg * 4);
-  B.val = reinterpret_cast<float *>(B.rid + p.Rpad);
+  B.Gm = B.W + HP;
+  B.gz2 = reinterpret_cast<float2 *>(B.Gm + (MODE != WM_FORWARD ? HP : 0));
+  B.gxs = reinterpret_cast<float *>(B.gz2) + ((2 * p.Hb + 3) & ~3);
+  B.sfast = reinterpret_cast<int *>(B.gxs + W4);
+  B.rid = B.sfast + ((nstrip + 3) & ~3);
+  B.roff = B.rid + p.Rpad;
+  B.val = reinterpret_cast<float *>(B.roff + p.Rpad);
   B.rb0 = p.rbstart[b];
   B.nrb = p.rbstart[b + 1] - B.rb0;
-  for (int q = tid; q < B.nrb; q += T) B.rid[q] = p.rperm[B.rb0 + q];
+  for (int q = tid; q < B.nrb; q += T) {
+    B.rid[q] = p.rperm[B.rb0 + q];
+    B.roff[q] = p.roff[B.rb0 + q];
+  }
   B.szr = (uint32_t)__cvta_generic_to_shared(Zr);
   B.has_up = b > 0;
   B.has_dn = b < p.Q - 1;
   for (int ph = 0; ph < 2; ++ph) {
-    B.su[ph] = (uint32_t)__cvta_generic_to_shared(B.U[ph]);
-    B.sup[ph] = B.has_up ? cluster_addr(B.su[ph], (uint32_t)(b - 1)) : 0u;
-    B.sdn[ph] = B.has_dn ? cluster_addr(B.su[ph], (uint32_t)(b + 1)) : 0u;
+    const uint32_t su = (uint32_t)__cvta_generic_to_shared(B.U[ph]);
+    B.sup[ph] = B.has_up ? cluster_addr(su, (uint32_t)(b - 1)) : 0u;
+    B.sdn[ph] = B.has_dn ? cluster_addr(su, (uint32_t)(b + 1)) : 0u;
   }
   for (int q = tid; q < p.PX; q += T) Zr[q] = 0.f;
-  for (int q = tid; q < p.Hb; q += T) B.gzs[q] = p.gz[b * p.Hb + q];
-  for (int q = tid; q < p.NXg * 4; q += T) B.gxs[q] = p.gx[q];
-  const int W4 = p.NXg * 4;
-  const size_t slab = (size_t)p.Q * p.Hb * W4;   // elements of one snapshot
+  for (int q = tid; q < p.Hb; q += T) {
+    const float g = p.gz[b * p.Hb + q];
+    B.gz2[q] = make_float2(g, g);
+  }
+  for (int q = tid; q < W4; q += T) B.gxs[q] = p.gx[q];
+  for (int q = tid; q < nstrip; q += T) {
+    int f = 1;
+    for (int r = q * V; r < q * V + V; ++r) f &= p.gz[b * p.Hb + r] == 1.f;
+    B.sfast[q] = f;
+  }
+  const size_t slab = (size_t)p.Q * HW;   // elements of one snapshot
 
   for (int item = cid; item < p.items; item += ncl) {
     const int pp = item / p.ipp;
@@ -644,8 +722,8 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
         w = __fmul_rn(c, c);
         cfl_bad |= !(w <= p.w_cfl);
       }
-      B.W[q] = w;
-      if (MODE != WM_FORWARD) B.Gm[q] = 0.f;
+      B.W[r * p.PX + 4 + x] = w;
+      if (MODE != WM_FORWARD) B.Gm[r * p.PX + 4 + x] = 0.f;
     }
     if (cfl_bad) atomicOr(p.status, 1);
 
@@ -663,32 +741,36 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
       }
       // ---------------- forward sweep
       band_zero(p, B, tid, T);
-      if (MODE == WM_GRADIENT) receiver_values<false, MODE>(p, B, tid, cid, s, pair, 0, 0);
-      cluster.sync();
+      step_fence();
       double jacc = 0.0;
       int ph = 0;
       for (int n = 0; n < p.N; ++n) {
         StepArgs a;
         a.ph = ph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
         a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
-        a.record = true; a.Jacc = &jacc; a.dnext = -1;
-        a.vnext_t = (MODE == WM_GRADIENT && n + 1 < p.N) ? n + 1 : -1;
+        a.record = MODE != WM_ADJOINT; a.Jacc = &jacc; a.dnext = -1;
+        a.vnext_t = MODE == WM_GRADIENT ? n : -1;
+        a.vnext_par = n & 1;
         if (MODE == WM_FORWARD || p.K > 1) {
           if (MODE != WM_FORWARD && n % p.K == 0) {
             band_copy(p, B, ph, p.CK + cid * p.CKslot + (size_t)(n / p.K) * 2 * slab +
-                                    (size_t)b * 2 * p.Hb * W4, true, tid, T);
+                                    (size_t)b * 2 * HW, true, tid, T);
             __syncthreads();   // the copy and the step map cells to threads differently
           }
           a.dofs = 0; a.sofs = 0;
           band_step<V, false, false, MODE, DT>(p, B, a, tid, T);
         } else {
-          a.dofs = (size_t)n * slab + (size_t)b * p.Hb * W4;
+          a.dofs = (size_t)n * slab + (size_t)b * HW;
           a.sofs = ((size_t)n * p.Q + b) * p.nwblk * V;
           band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
         }
-        cluster.sync();
+        step_fence();
         ph ^= 1;
       }
+      // the last level a^N is trace sample N-1
+      if (MODE != WM_ADJOINT)
+        record_receivers<MODE>(p, B, ph ? B.U[1] : B.U[0], p.N, pair, cid, &jacc, tid, T);
+      cluster_wait();
       if (MODE == WM_GRADIENT) {
         // CTA reduction of the squared residuals (deterministic order)
         __shared__ double red[32];
@@ -707,61 +789,67 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
 
       // ---------------- adjoint sweep
       band_zero(p, B, tid, T);
-      if (p.K == 1) receiver_values<true, MODE>(p, B, tid, cid, s, pair, p.N - 1, p.N & 1);
-      cluster.sync();
       ph = 0;
       if (p.K == 1) {
+        receiver_values<MODE>(p, B, tid, cid, pair, p.N - 1, p.N & 1);
+        step_fence();
         for (int k = p.N; k >= 1; --k) {
           StepArgs a;
           a.ph = ph; a.t = k; a.slot = cid; a.pair = pair; a.s = s;
           a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jacc = nullptr;
-          a.dofs = (size_t)(k - 1) * slab + (size_t)b * p.Hb * W4;
+          a.dofs = (size_t)(k - 1) * slab + (size_t)b * HW;
           a.sofs = ((size_t)(k - 1) * p.Q + b) * p.nwblk * V;
-          a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * p.Hb * W4) : -1;
+          a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * HW) : -1;
           a.vnext_t = k >= 2 ? k - 2 : -1;
+          a.vnext_par = (k - 1) & 1;
           band_step<V, true, true, MODE, DT>(p, B, a, tid, T);
-          cluster.sync();
+          step_fence();
           ph ^= 1;
         }
+        cluster_wait();
       } else {
-        float *AS = p.AS + cid * p.ASslot + (size_t)b * 2 * p.Hb * W4;
+        float *AS = p.AS + cid * p.ASslot + (size_t)b * 2 * HW;
+        step_fence();
+        cluster_wait();
         for (int j = p.nseg - 1; j >= 0; --j) {
           const int n0 = j * p.K, n1 = min(p.N, n0 + p.K);
           band_copy(p, B, ph, AS, true, tid, T);       // park mu^{k+1}, mu^{k+2}
           __syncthreads();
-          band_copy(p, B, 0, p.CK + cid * p.CKslot + (size_t)j * 2 * slab +
-                                 (size_t)b * 2 * p.Hb * W4, false, tid, T);
-          cluster.sync();
+          band_copy(p, B, 0, p.CK + cid * p.CKslot + (size_t)j * 2 * slab + (size_t)b * 2 * HW,
+                    false, tid, T);
+          step_fence();
           int fph = 0;
           for (int n = n0; n < n1; ++n) {              // recompute the segment
             StepArgs a;
             a.ph = fph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
             a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
-            a.record = false; a.Jacc = nullptr; a.dnext = -1; a.vnext_t = -1;
-            a.dofs = (size_t)(n - n0) * slab + (size_t)b * p.Hb * W4;
+            a.record = false; a.Jacc = nullptr; a.dnext = -1; a.vnext_t = -1; a.vnext_par = 0;
+            a.dofs = (size_t)(n - n0) * slab + (size_t)b * HW;
             a.sofs = ((size_t)(n - n0) * p.Q + b) * p.nwblk * V;
             band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
-            cluster.sync();
+            step_fence();
             fph ^= 1;
           }
+          cluster_wait();
           band_copy(p, B, 0, AS, false, tid, T);       // restore the adjoint state
-          receiver_values<true, MODE>(p, B, tid, cid, s, pair, n1 - 1, n1 & 1);
+          receiver_values<MODE>(p, B, tid, cid, pair, n1 - 1, n1 & 1);
           ph = 0;
-          cluster.sync();
+          step_fence();
           for (int k = n1; k > n0; --k) {
             StepArgs a;
             a.ph = ph; a.t = k; a.slot = cid; a.pair = pair; a.s = s;
             a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jacc = nullptr;
-            a.dofs = (size_t)(k - 1 - n0) * slab + (size_t)b * p.Hb * W4;
+            a.dofs = (size_t)(k - 1 - n0) * slab + (size_t)b * HW;
             a.sofs = ((size_t)(k - 1 - n0) * p.Q + b) * p.nwblk * V;
-            a.dnext = k - 2 >= n0 ? (long long)((size_t)(k - 2 - n0) * slab +
-                                                (size_t)b * p.Hb * W4)
+            a.dnext = k - 2 >= n0 ? (long long)((size_t)(k - 2 - n0) * slab + (size_t)b * HW)
                                   : -1;
             a.vnext_t = k - 1 > n0 ? k - 2 : -1;
+            a.vnext_par = (k - 1) & 1;
             band_step<V, true, true, MODE, DT>(p, B, a, tid, T);
-            cluster.sync();
+            step_fence();
             ph ^= 1;
           }
+          cluster_wait();
         }
       }
     }
@@ -771,7 +859,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
     for (int q = tid; q < HW; q += T) {
       const int r = q / W4, x = q - r * W4;
       const int z = b * p.Hb + r;
-      if (z < p.NZ && x < p.NX) GP[(size_t)z * p.NX + x] = B.Gm[q];
+      if (z < p.NZ && x < p.NX) GP[(size_t)z * p.NX + x] = B.Gm[r * p.PX + 4 + x];
     }
     cluster.sync();
     const int rows = (p.nz + p.Q - 1) / p.Q;
