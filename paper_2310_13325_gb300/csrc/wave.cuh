@@ -274,14 +274,18 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
 // band_step, just before the first strip that reads a neighbouring band or
 // overwrites rows a neighbour reads; the strips in between overlap the
 // cluster barrier. A run of steps is closed with cluster_wait().
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+// A thread that wrote no row a neighbouring band reads (it updated inner
+// strips only) arrives without release semantics: its writes are read
+// inside the CTA only, which the CTA barrier orders.
+__device__ __forceinline__ void cluster_arrive(bool release) {
+  if (release) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+  else asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
-__device__ __forceinline__ void step_fence() {
-  cluster_arrive();
+__device__ __forceinline__ void step_fence(bool release = true) {
+  cluster_arrive(release);
   __syncthreads();
 }
 
@@ -496,8 +500,10 @@ __device__ __forceinline__ void record_receivers(const WaveParams &p, const Band
 // before the wait on the previous step's cluster barrier. The strips at the
 // band edges follow the wait; their window rows beyond the band come from
 // the neighbouring bands' shared memory (or the zero row at the grid edge).
+// Returns whether the thread's warp reached the edge strips (its writes may
+// be read by a neighbouring band).
 template <int V, bool ADJ, bool SNAP, int MODE, class DT>
-__device__ __forceinline__ void band_step(const WaveParams &p, const Band &B,
+__device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
                                           const StepArgs &a, int tid, int T) {
   using M = typename MaskT<V>::type;
   const int Hb = p.Hb, PX = p.PX, NXg = p.NXg, W4 = NXg * 4;
@@ -600,12 +606,14 @@ __device__ __forceinline__ void band_step(const WaveParams &p, const Band &B,
     task_rows<V, ADJ, SNAP, MODE, DT>(a, c, rm, Dt, Dnt, St, Sw, vcur, PX, dn, dW, dG, W4, k1,
                                       k2, k3, k4, tid);
   }
+  const bool edge = waited;
   if (!waited) cluster_wait();
   if (fetch) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
       if (tid + u * T < B.nrb) B.val[a.vnext_par * p.Rpad + tid + u * T] = vnext[u];
   }
+  return edge;
 }
 
 // Value used at the receivers in the first step of an adjoint sweep (before
@@ -648,8 +656,12 @@ __device__ __forceinline__ void band_zero(const WaveParams &p, const Band &B, in
   for (int q = tid; q < n / 4; q += T) st4(B.U[0] + 4 * q, make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
-// Threads per CTA allowed for V rows per thread (register budget).
-template <int V> struct WaveMaxThreads { static constexpr int value = V >= 8 ? 448 : 512; };
+// Threads per CTA allowed for V rows per thread. The register file of an SM
+// is split over its 4 schedulers (16384 registers each), so 16, 14 and 12
+// warps leave 128, 128 and 168 registers per thread.
+template <int V> struct WaveMaxThreads {
+  static constexpr int value = V >= 10 ? 384 : (V >= 8 ? 448 : 512);
+};
 
 template <int V, int MODE, class DT>
 __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
@@ -744,6 +756,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
       step_fence();
       double jacc = 0.0;
       int ph = 0;
+      bool edge;
       for (int n = 0; n < p.N; ++n) {
         StepArgs a;
         a.ph = ph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
@@ -758,13 +771,13 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
             __syncthreads();   // the copy and the step map cells to threads differently
           }
           a.dofs = 0; a.sofs = 0;
-          band_step<V, false, false, MODE, DT>(p, B, a, tid, T);
+          edge = band_step<V, false, false, MODE, DT>(p, B, a, tid, T);
         } else {
           a.dofs = (size_t)n * slab + (size_t)b * HW;
           a.sofs = ((size_t)n * p.Q + b) * p.nwblk * V;
-          band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
+          edge = band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
         }
-        step_fence();
+        step_fence(edge);
         ph ^= 1;
       }
       // the last level a^N is trace sample N-1
@@ -802,8 +815,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
           a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * HW) : -1;
           a.vnext_t = k >= 2 ? k - 2 : -1;
           a.vnext_par = (k - 1) & 1;
-          band_step<V, true, true, MODE, DT>(p, B, a, tid, T);
-          step_fence();
+          step_fence(band_step<V, true, true, MODE, DT>(p, B, a, tid, T));
           ph ^= 1;
         }
         cluster_wait();
@@ -826,8 +838,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
             a.record = false; a.Jacc = nullptr; a.dnext = -1; a.vnext_t = -1; a.vnext_par = 0;
             a.dofs = (size_t)(n - n0) * slab + (size_t)b * HW;
             a.sofs = ((size_t)(n - n0) * p.Q + b) * p.nwblk * V;
-            band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
-            step_fence();
+            step_fence(band_step<V, false, true, MODE, DT>(p, B, a, tid, T));
             fph ^= 1;
           }
           cluster_wait();
@@ -845,8 +856,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
                                   : -1;
             a.vnext_t = k - 1 > n0 ? k - 2 : -1;
             a.vnext_par = (k - 1) & 1;
-            band_step<V, true, true, MODE, DT>(p, B, a, tid, T);
-            step_fence();
+            step_fence(band_step<V, true, true, MODE, DT>(p, B, a, tid, T));
             ph ^= 1;
           }
           cluster_wait();

@@ -13,7 +13,9 @@ const void *wave_kernel_f16(int V, int mode);
 const void *wave_kernel_fwd(int V);
 
 // Largest CTA size the kernel for V rows per thread is built for.
-inline int wave_max_threads(int V) { return V >= 8 ? 448 : 512; }
+inline int wave_max_threads(int V) {
+  return V >= 10 ? WaveMaxThreads<10>::value : (V >= 8 ? WaveMaxThreads<8>::value : WaveMaxThreads<4>::value);
+}
 
 template <class DT>
 const void *wave_kernel_table(int V, int mode) {
