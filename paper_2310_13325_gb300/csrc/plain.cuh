@@ -46,9 +46,9 @@ __global__ void plain_fwd_step(PlainParams q, const float *__restrict__ cur, flo
   if (r >= 0) {
     if (seis) seis[(size_t)r * q.N + n] = an;
     if (rho) {
-      const double res = (double)an - (double)dobs_s[(size_t)r * q.N + n];
-      rho[(size_t)r * q.N + n] = (float)(res * (double)rho_scale);
-      atomicAdd(J, res * res);
+      const float res = __fsub_rn(an, dobs_s[(size_t)r * q.N + n]);
+      rho[(size_t)r * q.N + n] = __fmul_rn(res, rho_scale);
+      atomicAdd(J, (double)res * (double)res);
     }
   }
 }

@@ -264,10 +264,6 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t cta_addr, uint32_t ran
   return r;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *ptr) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-}
-
 // Split cluster barrier. A time step ends with step_fence(): the arrive
 // publishes the step's shared-memory writes to the cluster, the CTA barrier
 // makes them visible inside the CTA. The matching wait comes inside the next
@@ -304,7 +300,7 @@ struct StepArgs {
   long long dnext;   // adjoint: element offset of the next step's slab (-1: none)
   int vnext_t;       // sample whose receiver values are fetched in this step (-1: none)
   int vnext_par;     // value slot they go to
-  double *Jacc;      // per-thread squared-residual accumulator
+  float *Jf;         // per-thread squared residuals of the last few steps (FP32)
 };
 
 // Receiver mask type of a task (4 bits per row).
@@ -465,21 +461,19 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
 #pragma unroll
     for (int k = 0; k < 8; ++k) win[k] = win[k + 1];
   }
-  // adjoint: pull the next step's snapshot rows of this task towards L2
-  if (ADJ && SNAP && Dnext && c.valid) {
-#pragma unroll
-    for (int i = 0; i < V; ++i) prefetch_l2(Dnext + (size_t)i * W4);
-  }
 }
 
 // Forward sweep: the level a^t held in lev is trace sample t-1. Traces
 // (forward modelling) or residuals against the observed sample, parked in
 // value slot (t-1)&1 by the thread that reads it here (gradient). The
-// adjoint-only mode records nothing.
+// residual r = d - d_obs and the adjoint source r dx^2/sigma^2 are rounded
+// to FP32 once each; r^2 is summed in FP32 over a few steps (Jf) and then
+// added to the FP64 misfit accumulator by the caller. The adjoint-only mode
+// records nothing.
 template <int MODE>
 __device__ __forceinline__ void record_receivers(const WaveParams &p, const Band &B,
                                                  const float *lev, int t, int pair, int slot,
-                                                 double *Jacc, int tid, int T) {
+                                                 float *Jf, int tid, int T) {
   const float *vrec = B.val + ((t - 1) & 1) * p.Rpad;
   for (int q = tid; q < B.nrb; q += T) {
     const int rr = B.rid[q];
@@ -487,10 +481,27 @@ __device__ __forceinline__ void record_receivers(const WaveParams &p, const Band
     if (MODE == WM_FORWARD) {
       p.seis[((size_t)pair * p.R + rr) * p.N + (t - 1)] = d;
     } else if (MODE == WM_GRADIENT) {
-      const double res = (double)d - (double)vrec[q];
-      *Jacc = __fma_rn(res, res, *Jacc);
-      p.rho[slot * p.rhoslot + (size_t)rr * p.N + (t - 1)] = (float)(res * (double)p.rho_scale);
+      const float res = __fsub_rn(d, vrec[q]);
+      *Jf = __fmaf_rn(res, res, *Jf);
+      p.rho[slot * p.rhoslot + (size_t)rr * p.N + (t - 1)] = __fmul_rn(res, p.rho_scale);
     }
+  }
+}
+
+// Pull a contiguous range of snapshot elements towards L2 (bulk prefetch in
+// 4 KB pieces, one per thread; only the 16-byte aligned interior).
+template <class DT>
+__device__ __forceinline__ void prefetch_slab_l2(const DT *p, size_t n, int tid, int T) {
+  uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p + n)) & ~(uintptr_t)15;
+  if (e <= a) return;
+  const size_t bytes = e - a;
+  const size_t piece = 4096;
+  for (size_t o = (size_t)tid * piece; o < bytes; o += (size_t)T * piece) {
+    const uint32_t sz = (uint32_t)min(piece, bytes - o);
+    asm volatile("{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %0;\n\t"
+                 "cp.async.bulk.prefetch.L2.global [g], %1;\n\t}" ::"l"(a + o), "r"(sz)
+                 : "memory");
   }
 }
 
@@ -519,7 +530,7 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
   float *Sp = Snap<DT>::scaled ? p.Dscale + a.slot * p.DSslot + a.sofs : nullptr;
   const float *vcur = B.val + (a.t & 1) * p.Rpad;
   if (!ADJ && a.record && a.t >= 1)
-    record_receivers<MODE>(p, B, cur, a.t, a.pair, a.slot, a.Jacc, tid, T);
+    record_receivers<MODE>(p, B, cur, a.t, a.pair, a.slot, a.Jf, tid, T);
   // receiver values of a later step are fetched now and parked in shared
   // memory at the end of this step, so no dependent global load sits on the
   // critical path of the receiver rows
@@ -541,6 +552,8 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
       }
     }
   }
+  // adjoint: pull the band's snapshot slab of the next step towards L2
+  if (ADJ && SNAP && Dn) prefetch_slab_l2(Dn, (size_t)Hb * W4, tid, T);
   const float2 k1 = make_float2(p.c1, p.c1), k2 = make_float2(p.c2, p.c2);
   const float2 k3 = make_float2(p.c3, p.c3), k4 = make_float2(p.c4, p.c4);
   const int nstrip = Hb / V;
@@ -755,13 +768,14 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
       band_zero(p, B, tid, T);
       step_fence();
       double jacc = 0.0;
+      float jf = 0.f;
       int ph = 0;
       bool edge;
       for (int n = 0; n < p.N; ++n) {
         StepArgs a;
         a.ph = ph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
         a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
-        a.record = MODE != WM_ADJOINT; a.Jacc = &jacc; a.dnext = -1;
+        a.record = MODE != WM_ADJOINT; a.Jf = &jf; a.dnext = -1;
         a.vnext_t = MODE == WM_GRADIENT ? n : -1;
         a.vnext_par = n & 1;
         if (MODE == WM_FORWARD || p.K > 1) {
@@ -779,10 +793,12 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
         }
         step_fence(edge);
         ph ^= 1;
+        if ((n & 15) == 15) { jacc += (double)jf; jf = 0.f; }
       }
       // the last level a^N is trace sample N-1
       if (MODE != WM_ADJOINT)
-        record_receivers<MODE>(p, B, ph ? B.U[1] : B.U[0], p.N, pair, cid, &jacc, tid, T);
+        record_receivers<MODE>(p, B, ph ? B.U[1] : B.U[0], p.N, pair, cid, &jf, tid, T);
+      jacc += (double)jf;
       cluster_wait();
       if (MODE == WM_GRADIENT) {
         // CTA reduction of the squared residuals (deterministic order)
@@ -809,7 +825,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
         for (int k = p.N; k >= 1; --k) {
           StepArgs a;
           a.ph = ph; a.t = k; a.slot = cid; a.pair = pair; a.s = s;
-          a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jacc = nullptr;
+          a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jf = nullptr;
           a.dofs = (size_t)(k - 1) * slab + (size_t)b * HW;
           a.sofs = ((size_t)(k - 1) * p.Q + b) * p.nwblk * V;
           a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * HW) : -1;
@@ -835,7 +851,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
             StepArgs a;
             a.ph = fph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
             a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
-            a.record = false; a.Jacc = nullptr; a.dnext = -1; a.vnext_t = -1; a.vnext_par = 0;
+            a.record = false; a.Jf = nullptr; a.dnext = -1; a.vnext_t = -1; a.vnext_par = 0;
             a.dofs = (size_t)(n - n0) * slab + (size_t)b * HW;
             a.sofs = ((size_t)(n - n0) * p.Q + b) * p.nwblk * V;
             step_fence(band_step<V, false, true, MODE, DT>(p, B, a, tid, T));
@@ -849,7 +865,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
           for (int k = n1; k > n0; --k) {
             StepArgs a;
             a.ph = ph; a.t = k; a.slot = cid; a.pair = pair; a.s = s;
-            a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jacc = nullptr;
+            a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jf = nullptr;
             a.dofs = (size_t)(k - 1 - n0) * slab + (size_t)b * HW;
             a.sofs = ((size_t)(k - 1 - n0) * p.Q + b) * p.nwblk * V;
             a.dnext = k - 2 >= n0 ? (long long)((size_t)(k - 2 - n0) * slab + (size_t)b * HW)

@@ -2,10 +2,13 @@
 the FP64 oracle, through the C ABI.
 
 Tolerances: relative L2 <= 1e-5 for FP32 traces and gradients driven by data
-residuals. The misfit (Eq. 26) is reduced in FP64: its reduction is held to
-1e-10 against an FP64 sum of the same GPU traces, and its value against the
-oracle to J_TOL, derived from the trace tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <=
-2 (|d| / |r|) rel(d) with |d| / |r| <= 1.5 for prior particles, so 3e-5.
+residuals. The misfit (Eq. 26) rounds each residual to FP32 once (2^-24), sums
+the squares of at most 64 residuals per thread in FP32 (4 receivers x 16
+steps: relative error <= 64 * 2^-24 ~ 3.8e-6) and accumulates those partial
+sums in FP64: the reduction is held to 4e-6 against an FP64 sum of the same
+GPU traces, and its value against the oracle to J_TOL, derived from the trace
+tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <= 2 (|d| / |r|) rel(d) with |d| / |r|
+<= 1.5 for prior particles, so 3e-5.
 Reduced-precision snapshots are measured and held to the bounds stated with
 each test.
 """
@@ -56,10 +59,11 @@ def test_gradient_and_misfit_match_oracle_cfg1():
     for p in range(2):
         assert rel(G[p], G_ref[p]) <= 1e-5, rel(G[p], G_ref[p])
     assert np.all(np.abs(J - J_ref) <= J_TOL * np.abs(J_ref)), (J, J_ref)
-    # the FP64 reduction itself, on the GPU's own traces
+    # the reduction itself, on the GPU's own traces, against an FP64 sum
     tr = fwi.forward(_t(V)).double().cpu().numpy()
     J_host = 0.5 * ((tr - d_obs.astype(np.float32)[None]) ** 2).sum(axis=(1, 2, 3)) / sigma ** 2
-    assert np.all(np.abs(J - J_host) <= 1e-10 * J_host), (J, J_host)
+    print("misfit reduction rel. error:", np.abs(J - J_host) / J_host)
+    assert np.all(np.abs(J - J_host) <= 4e-6 * J_host), (J, J_host)
 
 
 def test_plain_loop_equals_batched_bit_for_bit():
@@ -76,7 +80,9 @@ def test_plain_loop_equals_batched_bit_for_bit():
     Sp = fwi.forward(Vt)
     assert torch.equal(Sb, Sp)
     assert torch.equal(Gb, Gp)
-    assert torch.allclose(Jb, Jp, rtol=1e-12, atol=0)
+    # same FP32 residuals; the batched kernel sums their squares in FP32 over
+    # at most 64 terms before the FP64 accumulation (bound 64 * 2^-24)
+    assert torch.allclose(Jb, Jp, rtol=4e-6, atol=0)
 
 
 @pytest.mark.parametrize("K", [7, 50])
