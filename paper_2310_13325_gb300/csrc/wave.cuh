@@ -208,17 +208,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   return upk(r);
 }
 
-// Laplacian bracket of the cell pair (j, j+1): lf[k], rt[k] the neighbours at
-// distance k+1 to the left and right, up[k], dn[k] above and below, kN the
-// coefficient c_N in both lanes; same operation order per lane as lap_cell.
+// Laplacian bracket of the cell pair (j, j+1) from h[k], the sums of its
+// left and right neighbours at distance k+1, and up[k], dn[k], its
+// neighbours above and below; kN holds c_N in both lanes. Per lane the
+// operations are those of lap_cell: 4u is exact, so fma(-4, u, x) rounds
+// x - 4u exactly as the subtraction does.
 __device__ __forceinline__ float2 lap_pair(float2 k1, float2 k2, float2 k3, float2 k4, float2 u,
-                                           const float2 lf[4], const float2 rt[4],
-                                           const float2 up[4], const float2 dn[4]) {
-  const float2 u4 = mul2(make_float2(4.f, 4.f), u);
-  float2 s = mul2(k4, sub2(add2(add2(lf[3], rt[3]), add2(up[3], dn[3])), u4));
-  s = fma2(k3, sub2(add2(add2(lf[2], rt[2]), add2(up[2], dn[2])), u4), s);
-  s = fma2(k2, sub2(add2(add2(lf[1], rt[1]), add2(up[1], dn[1])), u4), s);
-  s = fma2(k1, sub2(add2(add2(lf[0], rt[0]), add2(up[0], dn[0])), u4), s);
+                                           const float2 h[4], const float2 up[4],
+                                           const float2 dn[4]) {
+  const float2 m4 = make_float2(-4.f, -4.f);
+  float2 s = mul2(k4, fma2(m4, u, add2(h[3], add2(up[3], dn[3]))));
+  s = fma2(k3, fma2(m4, u, add2(h[2], add2(up[2], dn[2]))), s);
+  s = fma2(k2, fma2(m4, u, add2(h[1], add2(up[1], dn[1]))), s);
+  s = fma2(k1, fma2(m4, u, add2(h[0], add2(up[0], dn[0]))), s);
   return s;
 }
 
@@ -374,17 +376,17 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
     else
       win[8] = c.bedge ? ld_cluster4(c.bot + (uint32_t)(i + 4 - V) * c.bstr) : ld4(rp + 4 * PX);
     const float4 Lf = ld4(rp - 4), Rf = ld4(rp + 4), C = win[4];
-    // cell pairs (0,1) and (2,3): neighbours at distance 1..4
+    // cell pairs (0,1) and (2,3). The horizontal neighbour sums are formed
+    // lane by lane (scalar adds land directly in register pairs; pairing the
+    // odd-offset neighbours instead would need register moves)
     const float2 c01 = make_float2(C.x, C.y), c23 = make_float2(C.z, C.w);
-    float2 lf01[4], rt01[4], lf23[4], rt23[4], up01[4], dn01[4], up23[4], dn23[4];
-    lf01[0] = make_float2(Lf.w, C.x);  rt01[0] = make_float2(C.y, C.z);
-    lf01[1] = make_float2(Lf.z, Lf.w); rt01[1] = make_float2(C.z, C.w);
-    lf01[2] = make_float2(Lf.y, Lf.z); rt01[2] = make_float2(C.w, Rf.x);
-    lf01[3] = make_float2(Lf.x, Lf.y); rt01[3] = make_float2(Rf.x, Rf.y);
-    lf23[0] = make_float2(C.y, C.z);   rt23[0] = make_float2(C.w, Rf.x);
-    lf23[1] = make_float2(C.x, C.y);   rt23[1] = make_float2(Rf.x, Rf.y);
-    lf23[2] = make_float2(Lf.w, C.x);  rt23[2] = make_float2(Rf.y, Rf.z);
-    lf23[3] = make_float2(Lf.z, Lf.w); rt23[3] = make_float2(Rf.z, Rf.w);
+    const float xs[12] = {Lf.x, Lf.y, Lf.z, Lf.w, C.x, C.y, C.z, C.w, Rf.x, Rf.y, Rf.z, Rf.w};
+    float2 h01[4], h23[4], up01[4], dn01[4], up23[4], dn23[4];
+#pragma unroll
+    for (int d = 1; d <= 4; ++d) {
+      h01[d - 1] = make_float2(__fadd_rn(xs[4 - d], xs[4 + d]), __fadd_rn(xs[5 - d], xs[5 + d]));
+      h23[d - 1] = make_float2(__fadd_rn(xs[6 - d], xs[6 + d]), __fadd_rn(xs[7 - d], xs[7 + d]));
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       up01[k] = make_float2(win[3 - k].x, win[3 - k].y);
@@ -392,8 +394,8 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
       up23[k] = make_float2(win[3 - k].z, win[3 - k].w);
       dn23[k] = make_float2(win[5 + k].z, win[5 + k].w);
     }
-    float2 s01 = lap_pair(k1, k2, k3, k4, c01, lf01, rt01, up01, dn01);
-    float2 s23 = lap_pair(k1, k2, k3, k4, c23, lf23, rt23, up23, dn23);
+    float2 s01 = lap_pair(k1, k2, k3, k4, c01, h01, up01, dn01);
+    float2 s23 = lap_pair(k1, k2, k3, k4, c23, h23, up23, dn23);
     if (c.special) {
       if (!ADJ) {
         if (c.srow == i) add_lane(s01, s23, c.slane, a.src_val);
