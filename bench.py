@@ -482,8 +482,13 @@ def main():
                      "frac": achieved / hbm, "traffic": traffic,
                      "kernel": "wave_cluster_kernel (fwi_gradient)",
                      "peak_source": src + " hbm_gbs",
+                     "dram_gbs": (traffic / (res["t_fwi_ms"] * 1e-3) / 1e9
+                                  if traffic else None),
+                     "dram_frac": (traffic / (res["t_fwi_ms"] * 1e-3) / 1e9 / hbm
+                                   if traffic else None),
                      "note": "algorithmic 16 B per cell update; the fields stay in shared "
-                             "memory, DRAM sees the stored snapshots only"},
+                             "memory, DRAM sees the stored snapshots only (traffic, "
+                             "dram_gbs: ncu bytes per launch scaled by cell updates)"},
         "gpu_launches": (2 + 24) * args.steps,
         "clocks": res["clocks"],
     }
