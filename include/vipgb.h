@@ -125,19 +125,24 @@ int  fwi_autotune(fwi_ctx *ctx, int P, int precision);
 
 /* Force the batched launch shape: Q CTAs per cluster (1..16, 0 = any), V
  * rows per thread (0 = any), T threads per CTA (multiple of 32,
- * 0 = any) and the number of sources one cluster processes per work item
- * (0 = any). V is one of 4, 5, 8, 10. All zeros restore automatic choice. A shape that does not fit
- * the device makes later calls return VIP_ERR_UNSUPPORTED. Traces and
- * misfits do not depend on the shape; gradients do not depend on Q, V, T
- * (every cell update and accumulation is evaluated identically) and are
- * deterministic for any split of the sources. */
-int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T, int sources_per_item);
+ * 0 = any), the number of sources one cluster processes per work item
+ * (0 = any) and where the model coefficients w' and the gradient
+ * accumulator live: coeff 1 = shared memory next to the wavefield, 2 =
+ * global memory (only the two time levels stay in shared memory, so taller
+ * bands and smaller clusters fit large grids), 0 = any. V is one of 4, 5, 8,
+ * 10 (10 only with coeff 1). All zeros restore automatic choice. A shape that
+ * does not fit the device makes later calls return VIP_ERR_UNSUPPORTED.
+ * Traces and misfits do not depend on the shape; gradients do not depend on
+ * Q, V, T or coeff (every cell update and accumulation is evaluated
+ * identically) and are deterministic for any split of the sources. */
+int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T, int sources_per_item, int coeff);
 int  fwi_set_autotune(fwi_ctx *ctx, int enable);
 
-/* Describe the plan chosen for P particles: writes up to 8 ints to plan_out
+/* Describe the plan chosen for P particles: writes 10 ints to plan_out
  * (host): {cluster_ctas, rows_per_thread, threads, band_rows, concurrent
- * pairs, ckpt_every, work_items, sources_per_item}, and the device bytes
- * the context holds after planning to bytes_out (host, may be NULL). */
+ * pairs, ckpt_every, work_items, sources_per_item, coeff (1 shared, 2
+ * global memory), shared-memory bytes per CTA}, and the device bytes the
+ * context holds after planning to bytes_out (host, may be NULL). */
 int  fwi_query_plan(fwi_ctx *ctx, int P, int precision, int *plan_out,
                     size_t *bytes_out);
 

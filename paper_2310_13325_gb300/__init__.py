@@ -96,23 +96,26 @@ class Fwi:
     def set_mode(self, mode=FWI_MODE_BATCHED, ckpt_every=1):
         check(self._L.fwi_set_mode(self._h, int(mode), int(ckpt_every)), "fwi_set_mode")
 
-    def set_plan(self, Q=0, V=0, T=0, sources_per_item=0):
+    def set_plan(self, Q=0, V=0, T=0, sources_per_item=0, coeff=0):
         """Force the batched launch shape (cluster CTAs, rows per thread,
-        threads per CTA, sources per work item); zeros = automatic."""
-        check(self._L.fwi_set_plan(self._h, int(Q), int(V), int(T), int(sources_per_item)),
-              "fwi_set_plan")
+        threads per CTA, sources per work item, coefficients in shared (1) or
+        global (2) memory); zeros = automatic."""
+        check(self._L.fwi_set_plan(self._h, int(Q), int(V), int(T), int(sources_per_item),
+                                   int(coeff)), "fwi_set_plan")
 
     def set_autotune(self, enable=True):
         check(self._L.fwi_set_autotune(self._h, int(bool(enable))), "fwi_set_autotune")
 
     def query_plan(self, P, precision=FWI_FP32):
-        out = (ctypes.c_int * 8)()
+        out = (ctypes.c_int * 10)()
         nb = ctypes.c_size_t()
         check(self._L.fwi_query_plan(self._h, int(P), int(precision), out,
                                      ctypes.byref(nb)), "fwi_query_plan")
         keys = ("cluster_ctas", "rows_per_thread", "threads", "band_rows",
                 "concurrent_pairs", "ckpt_every", "work_items", "sources_per_item")
         d = dict(zip(keys, list(out)))
+        d["coefficients"] = "global" if out[8] == 2 else "shared"
+        d["smem_bytes"] = out[9]
         d["scratch_bytes"] = nb.value
         return d
 

@@ -31,7 +31,7 @@ _SIGS = {
     "fwi_destroy": (None, [c_void_p]),
     "fwi_set_mode": (c_int, [c_void_p, c_int, c_int]),
     "fwi_set_autotune": (c_int, [c_void_p, c_int]),
-    "fwi_set_plan": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
+    "fwi_set_plan": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int]),
     "fwi_autotune": (c_int, [c_void_p, c_int, c_int]),
     "fwi_query_plan": (c_int, [c_void_p, c_int, c_int, c_int_p, ctypes.POINTER(c_size_t)]),
     "fwi_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),

@@ -40,6 +40,8 @@ struct Plan {
   int K = 1, nseg = 1;
   int items = 0, ipp = 1, spi = 1;
   size_t Dslot = 0, DSslot = 0, rhoslot = 0, GPslot = 0, CKslot = 0, ASslot = 0;
+  size_t Wgslot = 0, Ggslot = 0;
+  bool gw = false;   // w' and the accumulator in global memory
   size_t slot_bytes = 0, total_bytes = 0;
   int mode = 0, dtype = 0;
   double est = 0;
@@ -78,8 +80,9 @@ struct fwi_ctx {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
-  std::map<std::tuple<int, int, int>, std::array<int, 3>> tuned;   // (P,mode,dtype) -> Q,V,T
+  std::map<std::tuple<int, int, int>, std::array<int, 4>> tuned;   // (P,mode,dtype) -> Q,V,T,gw
   int force_Q = 0, force_V = 0, force_T = 0, force_spi = 0;          // launch override
+  int force_coeff = 0;   // 0 any, 1 coefficients in shared memory, 2 in global memory
   int use_graphs = 1;   // VIPGB_GRAPHS=0 in the environment: eager launches
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
@@ -89,11 +92,11 @@ struct fwi_ctx {
 
 namespace vip {
 
-static const void *kernel_ptr(int V, int mode, int dtype) {
-  if (mode == WM_FORWARD) return wave_kernel_f32(V, mode);
-  if (dtype == FWI_FP32) return wave_kernel_f32(V, mode);
-  if (dtype == FWI_CKPT_BF16) return wave_kernel_bf16(V, mode);
-  if (dtype == FWI_CKPT_FP16) return wave_kernel_f16(V, mode);
+static const void *kernel_ptr(int V, int mode, int dtype, bool gw) {
+  if (mode == WM_FORWARD) return wave_kernel_f32(V, mode, gw);
+  if (dtype == FWI_FP32) return wave_kernel_f32(V, mode, gw);
+  if (dtype == FWI_CKPT_BF16) return wave_kernel_bf16(V, mode, gw);
+  if (dtype == FWI_CKPT_FP16) return wave_kernel_f16(V, mode, gw);
   return nullptr;
 }
 
@@ -107,12 +110,13 @@ static int band_height(int NZ, int Q, int V) {
 static int receiver_pad(int R) { return (R + 3) & ~3; }
 
 // Shared memory of the batched kernel (floats): two levels, the zero row, w'
-// and (gradient) the accumulator, all [Hb][PX]; (gz, gz) per row; the
+// and (gradient) the accumulator, all [Hb][PX] (w' and the accumulator are
+// left out when they live in global memory, gw); (gz, gz) per row; the
 // column taper; one flag per strip; receiver numbers, cell offsets and two
 // value slots.
-static size_t wave_smem(int Hb, int V, int PX, int NXg, bool grad, int R) {
+static size_t wave_smem(int Hb, int V, int PX, int NXg, bool grad, int R, bool gw) {
   const size_t HP = (size_t)Hb * PX;
-  size_t f = (grad ? 4 : 3) * HP + PX + ((2 * Hb + 3) & ~3) + (size_t)NXg * 4 +
+  size_t f = (gw ? 2 : (grad ? 4 : 3)) * HP + PX + ((2 * Hb + 3) & ~3) + (size_t)NXg * 4 +
              ((Hb / V + 3) & ~3) + 4 * (size_t)receiver_pad(R);
   return f * 4;
 }
@@ -197,11 +201,13 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
   const size_t slab = (size_t)pl.Q * pl.Hb * W4;
   const bool grad = pl.mode != WM_FORWARD;
   pl.Dslot = pl.DSslot = pl.rhoslot = pl.GPslot = pl.CKslot = pl.ASslot = 0;
+  pl.Wgslot = pl.gw ? slab : 0;
+  pl.Ggslot = (pl.gw && grad) ? slab : 0;
   if (grad) {
     const int steps = pl.K == 1 ? c->N : pl.K;
     pl.Dslot = (size_t)steps * slab;
     if (pl.dtype == FWI_CKPT_FP16) pl.DSslot = (size_t)steps * pl.Q * pl.nwblk * pl.V;
-    pl.GPslot = (size_t)c->NZ * c->NX;
+    pl.GPslot = pl.gw ? 0 : (size_t)c->NZ * c->NX;   // gw: the fold reads the accumulator
     if (pl.mode == WM_GRADIENT) pl.rhoslot = (size_t)c->R * c->N;
     if (pl.K > 1) {
       pl.nseg = idiv_up(c->N, pl.K);
@@ -214,7 +220,8 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
   // keep every slot 256-byte aligned
   auto a = [](size_t n, size_t es) { return align_up(n * es, 256); };
   pl.slot_bytes = a(pl.Dslot, dtype_size(pl.dtype)) + a(pl.DSslot, 4) + a(pl.rhoslot, 4) +
-                  a(pl.GPslot, 4) + a(pl.CKslot, 4) + a(pl.ASslot, 4);
+                  a(pl.GPslot, 4) + a(pl.CKslot, 4) + a(pl.ASslot, 4) + a(pl.Wgslot, 4) +
+                  a(pl.Ggslot, 4);
   const size_t gi = (pl.mode != WM_FORWARD && pl.ipp > 1)
                         ? align_up((size_t)P * pl.ipp * c->nz * c->nx * 4, 256) : 0;
   pl.total_bytes = align_up((size_t)P * c->S * pl.Q * 8, 256) + gi +
@@ -224,8 +231,11 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
 static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<Plan> &out) {
   const bool grad = mode != WM_FORWARD;
   const int Vs[4] = {4, 5, 8, 10};
+  for (int gwi = 0; gwi < 2; ++gwi)
   for (int V : Vs) {
-    const void *fn = kernel_ptr(V, mode, dtype);
+    const bool gw = gwi == 1;
+    if (c->force_coeff && c->force_coeff != (gw ? 2 : 1)) continue;
+    const void *fn = kernel_ptr(V, mode, dtype, gw);
     if (!fn) continue;
     cudaFuncAttributes fa;
     VIP_TRY(cudaFuncGetAttributes(&fa, fn));
@@ -235,13 +245,13 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
       if (Hb < 4) continue;
       const int NXg = idiv_up(c->NX, 4);
       const int PX = 4 * (NXg + 2);
-      const size_t smem = wave_smem(Hb, V, PX, NXg, grad, c->R);
+      const size_t smem = wave_smem(Hb, V, PX, NXg, grad, c->R, gw);
       if (smem + fa.sharedSizeBytes > c->smem_optin) continue;
       const int ntask = (Hb / V) * NXg;
       const int ntask_pad = idiv_up(ntask, 32) * 32;
       // threads per CTA: whole numbers of tasks per thread (1, 2, 3) where
       // possible, rounded up to warps, within the kernel's register budget
-      const int Tmax = wave_max_threads(V);
+      const int Tmax = wave_max_threads(V, gw);
       int Ts[4] = {ntask_pad, idiv_up(idiv_up(ntask_pad, 2), 32) * 32,
                    idiv_up(idiv_up(ntask_pad, 3), 32) * 32, c->force_T};
       for (int ti = 0; ti < 4; ++ti) {
@@ -254,7 +264,7 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
         Plan pl;
         pl.Q = Q; pl.V = V; pl.T = T; pl.Hb = Hb; pl.NXg = NXg; pl.PX = PX;
         pl.ntask = ntask; pl.ntask_pad = ntask_pad; pl.nwblk = ntask_pad / 32;
-        pl.smem = smem; pl.mode = mode; pl.dtype = dtype;
+        pl.smem = smem; pl.mode = mode; pl.dtype = dtype; pl.gw = gw;
         VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (Q > 8) VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         cudaLaunchConfig_t cfg = {};
@@ -289,7 +299,9 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
         // plus a fixed barrier cost
         const double tpt = (double)idiv_up(ntask_pad, T);
         const double per_step = tpt * (V + 3.0) + 6.0;
-        pl.est = best * per_step * (grad ? 2.0 : 1.0);
+        // coefficients in global memory: every row also loads w' (and in the
+        // adjoint reads and writes the accumulator) through L1/L2
+        pl.est = best * per_step * (grad ? 2.0 : 1.0) * (gw ? 1.25 : 1.0);
         out.push_back(pl);
       }
     }
@@ -332,7 +344,9 @@ static int choose_plan(fwi_ctx *c, int P, int mode, int dtype, Plan &out) {
     if (!pick) return VIP_ERR_UNSUPPORTED;
   } else if (it != c->tuned.end()) {
     for (auto &p : cand)
-      if (p.Q == it->second[0] && p.V == it->second[1] && p.T == it->second[2]) pick = &p;
+      if (p.Q == it->second[0] && p.V == it->second[1] && p.T == it->second[2] &&
+          (int)p.gw == it->second[3])
+        pick = &p;
   }
   if (!pick) {
     pick = &cand[0];
@@ -422,15 +436,17 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   wp.GP = (float *)sub(pl.GPslot, 4);
   wp.CK = (float *)sub(pl.CKslot, 4);
   wp.AS = (float *)sub(pl.ASslot, 4);
+  wp.Wg = (float *)sub(pl.Wgslot, 4);
+  wp.Gg = (float *)sub(pl.Ggslot, 4);
   const size_t sb = pl.slot_bytes;
   wp.Dslot = sb / dtype_size(pl.dtype);
   wp.DSslot = sb / 4; wp.rhoslot = sb / 4; wp.GPslot = sb / 4; wp.CKslot = sb / 4;
-  wp.ASslot = sb / 4;
+  wp.ASslot = sb / 4; wp.Wgslot = sb / 4; wp.Ggslot = sb / 4;
   return cv.ok() ? VIP_OK : VIP_ERR_NOMEM;
 }
 
 static int prepare_wave(const Plan &pl) {
-  const void *fn = kernel_ptr(pl.V, pl.mode, pl.dtype);
+  const void *fn = kernel_ptr(pl.V, pl.mode, pl.dtype, pl.gw);
   if (!fn) return VIP_ERR_UNSUPPORTED;
   VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   if (pl.Q > 8) VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -438,7 +454,7 @@ static int prepare_wave(const Plan &pl) {
 }
 
 static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream_t st) {
-  const void *fn = kernel_ptr(pl.V, pl.mode, pl.dtype);
+  const void *fn = kernel_ptr(pl.V, pl.mode, pl.dtype, pl.gw);
   if (!fn) return VIP_ERR_UNSUPPORTED;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ncl * pl.Q, 1, 1);
@@ -564,7 +580,7 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
   VIP_TRY(cudaEventCreate(&e0));
   VIP_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  std::array<int, 3> pick = {cand[0].Q, cand[0].V, cand[0].T};
+  std::array<int, 4> pick = {cand[0].Q, cand[0].V, cand[0].T, (int)cand[0].gw};
   c->N = Ntune;
   for (auto &pl0 : cand) {
     Plan pl = pl0;
@@ -594,7 +610,7 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
     VIP_TRY(cudaEventElapsedTime(&ms, e0, e1));
     // normalise by the full problem's number of waves
     const float score = (float)(ms * idiv_up(pl0.items, pl0.ncl));
-    if (score < best) { best = score; pick = {pl.Q, pl.V, pl.T}; }
+    if (score < best) { best = score; pick = {pl.Q, pl.V, pl.T, (int)pl.gw}; }
   }
   c->N = Nsave;
   cudaEventDestroy(e0);
@@ -896,12 +912,12 @@ int fwi_set_mode(fwi_ctx *c, int mode, int ckpt_every) {
   return VIP_OK;
 }
 
-int fwi_set_plan(fwi_ctx *c, int Q, int V, int T, int sources_per_item) {
+int fwi_set_plan(fwi_ctx *c, int Q, int V, int T, int sources_per_item, int coeff) {
   if (!c || Q < 0 || Q > 16 || (V != 0 && V != 4 && V != 5 && V != 8 && V != 10) || T < 0 ||
-      T > 512 || (T % 32) ||
-      sources_per_item < 0)
+      T > 512 || (T % 32) || sources_per_item < 0 || coeff < 0 || coeff > 2)
     return VIP_ERR_ARG;
   c->force_Q = Q; c->force_V = V; c->force_T = T; c->force_spi = sources_per_item;
+  c->force_coeff = coeff;
   return VIP_OK;
 }
 
@@ -925,6 +941,7 @@ int fwi_query_plan(fwi_ctx *c, int P, int precision, int *plan_out, size_t *byte
   if (rc) return rc;
   plan_out[0] = pl.Q; plan_out[1] = pl.V; plan_out[2] = pl.T; plan_out[3] = pl.Hb;
   plan_out[4] = pl.ncl; plan_out[5] = pl.K; plan_out[6] = pl.items; plan_out[7] = pl.spi;
+  plan_out[8] = pl.gw ? 2 : 1; plan_out[9] = (int)pl.smem;
   if (bytes_out) *bytes_out = pl.total_bytes;
   return VIP_OK;
 }

@@ -91,6 +91,11 @@ struct WaveParams {
   float *GP;    size_t GPslot;   // [NZ][NX] gradient gather per slot
   float *CK;    size_t CKslot;   // restart checkpoints per slot
   float *AS;    size_t ASslot;   // parked adjoint state per slot
+  // coefficients in global memory (kernels built with GW): w' and the
+  // gradient accumulator per slot, [Q][Hb][NXg*4], so that the CTA's shared
+  // memory holds only the two time levels and a taller band fits
+  float *Wg;    size_t Wgslot;
+  float *Gg;    size_t Ggslot;
 };
 
 // ---------------------------------------------------------------------------
@@ -334,17 +339,27 @@ __device__ __forceinline__ void add_lane(float2 &s01, float2 &s23, int j, float 
 
 // The V rows of one task, 4 adjacent cells per row, top to bottom. Offsets
 // (floats) from c.cur: dn to the next level, dW to w', dG to the gradient
-// accumulator; PX is the row pitch of all four. The vertical stencil window
-// of 9 rows lives in registers; each row loads one new window row, its left
-// and right neighbour quadruples, w' and the previous value.
-template <int V, bool ADJ, bool SNAP, int MODE, class DT>
+// accumulator; PX is the row pitch of all four. With GW, w' and the
+// accumulator are instead read from global memory at wg, gg (row r0 of the
+// task, rows W4 apart), two rows ahead of their use. The vertical stencil
+// window of 9 rows lives in registers; each row loads one new window row, its
+// left and right neighbour quadruples, w' and the previous value.
+template <int V, bool ADJ, bool SNAP, int MODE, class DT, bool GW>
 __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
                                           typename MaskT<V>::type rm, DT *Dtask,
                                           const DT *Dnext, const float *Stask, float *Sw,
                                           const float *vcur, int PX, int dn, int dW, int dG,
-                                          int W4, float2 k1, float2 k2, float2 k3, float2 k4,
-                                          int tid) {
+                                          const float *wg, float *gg, int W4, float2 k1,
+                                          float2 k2, float2 k3, float2 k4, int tid) {
   using M = typename MaskT<V>::type;
+  float4 wq[V], gq[V];
+  if (GW) {
+#pragma unroll
+    for (int i = 0; i < 2 && i < V; ++i) {
+      wq[i] = ld4(wg + i * W4);
+      if (ADJ && SNAP) gq[i] = __ldcg(reinterpret_cast<const float4 *>(gg + i * W4));
+    }
+  }
   // adjoint: snapshot rows are loaded two rows ahead of their use
   float4 dq[V];
   float dinv[V];
@@ -369,6 +384,10 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
     if (ADJ && SNAP && i + 2 < V) {
       dinv[i + 2] = Snap<DT>::scaled ? Stask[i + 2] : 1.f;
       dq[i + 2] = Snap<DT>::ld(Dtask, (size_t)(i + 2) * W4, 1.f);
+    }
+    if (GW && i + 2 < V) {
+      wq[i + 2] = ld4(wg + (i + 2) * W4);
+      if (ADJ && SNAP) gq[i + 2] = __ldcg(reinterpret_cast<const float4 *>(gg + (i + 2) * W4));
     }
     float *rp = cp + i * PX;
     if (i + 4 < V)
@@ -410,7 +429,7 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
         }
       }
     }
-    const float4 Wv = ld4(rp + dW);
+    const float4 Wv = GW ? wq[i] : ld4(rp + dW);
     const float4 AP = ld4(rp + dn);
     const float2 wa = make_float2(Wv.x, Wv.y), wb = make_float2(Wv.z, Wv.w);
     const float2 pa = make_float2(AP.x, AP.y), pb = make_float2(AP.z, AP.w);
@@ -448,8 +467,8 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
       } else if (c.valid) {
         const float4 dv = dq[i];
         const float inv = dinv[i];
-        float *gp = rp + dG;
-        const float4 gm = ld4(gp);
+        float *gp = GW ? gg + i * W4 : rp + dG;
+        const float4 gm = GW ? gq[i] : ld4(gp);
         float2 da = make_float2(dv.x, dv.y), db = make_float2(dv.z, dv.w);
         if (Snap<DT>::scaled) {
           da = mul2(da, make_float2(inv, inv));
@@ -457,7 +476,8 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
         }
         const float2 ga2 = fma2(na, da, make_float2(gm.x, gm.y));
         const float2 gb2 = fma2(nb, db, make_float2(gm.z, gm.w));
-        st4(gp, make_float4(ga2.x, ga2.y, gb2.x, gb2.y));
+        if (GW) __stcg(reinterpret_cast<float4 *>(gp), make_float4(ga2.x, ga2.y, gb2.x, gb2.y));
+        else st4(gp, make_float4(ga2.x, ga2.y, gb2.x, gb2.y));
       }
     }
 #pragma unroll
@@ -515,14 +535,18 @@ __device__ __forceinline__ void prefetch_slab_l2(const DT *p, size_t n, int tid,
 // the neighbouring bands' shared memory (or the zero row at the grid edge).
 // Returns whether the thread's warp reached the edge strips (its writes may
 // be read by a neighbouring band).
-template <int V, bool ADJ, bool SNAP, int MODE, class DT>
+template <int V, bool ADJ, bool SNAP, int MODE, class DT, bool GW>
 __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
                                           const StepArgs &a, int tid, int T) {
   using M = typename MaskT<V>::type;
   const int Hb = p.Hb, PX = p.PX, NXg = p.NXg, W4 = NXg * 4;
   float *cur = a.ph ? B.U[1] : B.U[0];
   float *nxt = a.ph ? B.U[0] : B.U[1];
-  const int dn = (int)(nxt - cur), dW = (int)(B.W - cur), dG = (int)(B.Gm - cur);
+  const int dn = (int)(nxt - cur);
+  const int dW = GW ? 0 : (int)(B.W - cur), dG = GW ? 0 : (int)(B.Gm - cur);
+  // GW: this band's w' and accumulator in the cluster's slot
+  const float *Wgb = GW ? p.Wg + a.slot * p.Wgslot + (size_t)B.b * Hb * W4 : nullptr;
+  float *Ggb = GW ? p.Gg + a.slot * p.Ggslot + (size_t)B.b * Hb * W4 : nullptr;
   const uint32_t up_s = a.ph ? B.sup[1] : B.sup[0];
   const uint32_t dn_s = a.ph ? B.sdn[1] : B.sdn[0];
   const uint32_t rowb = (uint32_t)PX * 4u;
@@ -618,8 +642,10 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
     const DT *Dnt = Dn ? Dn + toff : nullptr;
     const float *St = Sp ? Sp + (task0 / 32) * V : nullptr;
     float *Sw = Sp ? Sp + (task0 / 32) * V : nullptr;
-    task_rows<V, ADJ, SNAP, MODE, DT>(a, c, rm, Dt, Dnt, St, Sw, vcur, PX, dn, dW, dG, W4, k1,
-                                      k2, k3, k4, tid);
+    task_rows<V, ADJ, SNAP, MODE, DT, GW>(a, c, rm, Dt, Dnt, St, Sw, vcur, PX, dn, dW, dG,
+                                          GW ? Wgb + toff : nullptr,
+                                          (GW && ADJ) ? Ggb + toff : nullptr, W4, k1, k2, k3,
+                                          k4, tid);
   }
   const bool edge = waited;
   if (!waited) cluster_wait();
@@ -673,13 +699,14 @@ __device__ __forceinline__ void band_zero(const WaveParams &p, const Band &B, in
 
 // Threads per CTA allowed for V rows per thread. The register file of an SM
 // is split over its 4 schedulers (16384 registers each), so 16, 14 and 12
-// warps leave 128, 128 and 168 registers per thread.
-template <int V> struct WaveMaxThreads {
-  static constexpr int value = V >= 10 ? 384 : (V >= 8 ? 448 : 512);
+// warps leave 128, 128 and 168 registers per thread. The global-coefficient
+// kernels keep two rows of w' and of the accumulator in flight and take 12.
+template <int V, bool GW = false> struct WaveMaxThreads {
+  static constexpr int value = (V >= 10 || GW) ? 384 : (V >= 8 ? 448 : 512);
 };
 
-template <int V, int MODE, class DT>
-__global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
+template <int V, int MODE, class DT, bool GW>
+__global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
     wave_cluster_kernel(const __grid_constant__ WaveParams p) {
   cg::cluster_group cluster = cg::this_cluster();
   const int b = (int)cluster.block_rank();
@@ -696,9 +723,9 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
   B.U[0] = smem;
   B.U[1] = smem + HP;
   float *Zr = smem + 2 * HP;
-  B.W = Zr + p.PX;
-  B.Gm = B.W + HP;
-  B.gz2 = reinterpret_cast<float2 *>(B.Gm + (MODE != WM_FORWARD ? HP : 0));
+  B.W = GW ? nullptr : Zr + p.PX;
+  B.Gm = GW ? nullptr : B.W + HP;
+  B.gz2 = reinterpret_cast<float2 *>(GW ? Zr + p.PX : B.Gm + (MODE != WM_FORWARD ? HP : 0));
   B.gxs = reinterpret_cast<float *>(B.gz2) + ((2 * p.Hb + 3) & ~3);
   B.sfast = reinterpret_cast<int *>(B.gxs + W4);
   B.rid = B.sfast + ((nstrip + 3) & ~3);
@@ -749,8 +776,13 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
         w = __fmul_rn(c, c);
         cfl_bad |= !(w <= p.w_cfl);
       }
-      B.W[r * p.PX + 4 + x] = w;
-      if (MODE != WM_FORWARD) B.Gm[r * p.PX + 4 + x] = 0.f;
+      if (GW) {
+        p.Wg[(size_t)cid * p.Wgslot + (size_t)b * HW + q] = w;
+        if (MODE != WM_FORWARD) p.Gg[(size_t)cid * p.Ggslot + (size_t)b * HW + q] = 0.f;
+      } else {
+        B.W[r * p.PX + 4 + x] = w;
+        if (MODE != WM_FORWARD) B.Gm[r * p.PX + 4 + x] = 0.f;
+      }
     }
     if (cfl_bad) atomicOr(p.status, 1);
 
@@ -787,11 +819,11 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
             __syncthreads();   // the copy and the step map cells to threads differently
           }
           a.dofs = 0; a.sofs = 0;
-          edge = band_step<V, false, false, MODE, DT>(p, B, a, tid, T);
+          edge = band_step<V, false, false, MODE, DT, GW>(p, B, a, tid, T);
         } else {
           a.dofs = (size_t)n * slab + (size_t)b * HW;
           a.sofs = ((size_t)n * p.Q + b) * p.nwblk * V;
-          edge = band_step<V, false, true, MODE, DT>(p, B, a, tid, T);
+          edge = band_step<V, false, true, MODE, DT, GW>(p, B, a, tid, T);
         }
         step_fence(edge);
         ph ^= 1;
@@ -833,7 +865,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
           a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * HW) : -1;
           a.vnext_t = k >= 2 ? k - 2 : -1;
           a.vnext_par = (k - 1) & 1;
-          step_fence(band_step<V, true, true, MODE, DT>(p, B, a, tid, T));
+          step_fence(band_step<V, true, true, MODE, DT, GW>(p, B, a, tid, T));
           ph ^= 1;
         }
         cluster_wait();
@@ -856,7 +888,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
             a.record = false; a.Jf = nullptr; a.dnext = -1; a.vnext_t = -1; a.vnext_par = 0;
             a.dofs = (size_t)(n - n0) * slab + (size_t)b * HW;
             a.sofs = ((size_t)(n - n0) * p.Q + b) * p.nwblk * V;
-            step_fence(band_step<V, false, true, MODE, DT>(p, B, a, tid, T));
+            step_fence(band_step<V, false, true, MODE, DT, GW>(p, B, a, tid, T));
             fph ^= 1;
           }
           cluster_wait();
@@ -874,7 +906,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
                                   : -1;
             a.vnext_t = k - 1 > n0 ? k - 2 : -1;
             a.vnext_par = (k - 1) & 1;
-            step_fence(band_step<V, true, true, MODE, DT>(p, B, a, tid, T));
+            step_fence(band_step<V, true, true, MODE, DT, GW>(p, B, a, tid, T));
             ph ^= 1;
           }
           cluster_wait();
@@ -883,11 +915,15 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
     }
     if (MODE == WM_FORWARD) continue;
     // ---------------- gather the accumulator and fold onto the physical grid
-    float *GP = p.GP + cid * p.GPslot;
-    for (int q = tid; q < HW; q += T) {
-      const int r = q / W4, x = q - r * W4;
-      const int z = b * p.Hb + r;
-      if (z < p.NZ && x < p.NX) GP[(size_t)z * p.NX + x] = B.Gm[r * p.PX + 4 + x];
+    // (GW: the accumulator already sits in global memory, rows W4 apart)
+    float *GP = GW ? p.Gg + cid * p.Ggslot : p.GP + cid * p.GPslot;
+    const int gpitch = GW ? W4 : p.NX;
+    if (!GW) {
+      for (int q = tid; q < HW; q += T) {
+        const int r = q / W4, x = q - r * W4;
+        const int z = b * p.Hb + r;
+        if (z < p.NZ && x < p.NX) GP[(size_t)z * p.NX + x] = B.Gm[r * p.PX + 4 + x];
+      }
     }
     cluster.sync();
     const int rows = (p.nz + p.Q - 1) / p.Q;
@@ -900,7 +936,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V>::value, 1)
       const int xb = ix == p.nx - 1 ? p.NX - 1 : ix + p.nb;
       double acc = 0.0;
       for (int z = za; z <= zb; ++z)
-        for (int x = xa; x <= xb; ++x) acc += (double)GP[(size_t)z * p.NX + x];
+        for (int x = xa; x <= xb; ++x) acc += (double)GP[(size_t)z * gpitch + x];
       const float vv = vp[(size_t)iz * p.nx + ix];
       const float val = (float)(acc * 2.0 / ((double)vv * (double)p.dx2));
       if (p.grad_atomic) p.GI[((size_t)item * p.nz + iz) * p.nx + ix] = val;

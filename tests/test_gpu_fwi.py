@@ -111,18 +111,21 @@ def test_ragged_grid_every_launch_shape_agrees_with_oracle():
     fwi = vg.Fwi.from_config(cfg, geo)
     Vt, Dt = _t(V), _t(d_obs)
     base = None
-    shapes = [(1, 4, 0), (2, 4, 0), (3, 8, 0), (5, 4, 64), (7, 4, 0), (2, 8, 96)]
-    for Q, Vr, T in shapes:
-        fwi.set_plan(Q, Vr, T)
+    # (Q, V, T, coefficients: 1 shared memory, 2 global memory)
+    shapes = [(1, 4, 0, 1), (2, 4, 0, 1), (3, 8, 0, 1), (5, 4, 64, 1), (7, 4, 0, 1),
+              (2, 8, 96, 1), (1, 5, 0, 2), (3, 8, 0, 2), (4, 4, 64, 2), (2, 8, 96, 2)]
+    for Q, Vr, T, co in shapes:
+        fwi.set_plan(Q, Vr, T, coeff=co)
+        assert fwi.query_plan(3)["coefficients"] == ("global" if co == 2 else "shared")
         J, G = fwi.gradient(Vt, Dt, sigma)
         G = G.reshape(3, -1).cpu().numpy()
         for p in range(3):
-            assert rel(G[p], G_ref[p]) <= 1e-5, (Q, Vr, T, p, rel(G[p], G_ref[p]))
+            assert rel(G[p], G_ref[p]) <= 1e-5, (Q, Vr, T, co, p, rel(G[p], G_ref[p]))
         assert np.all(np.abs(J.cpu().numpy() - J_ref) <= J_TOL * J_ref)
         if base is None:
             base = G
         else:
-            assert np.array_equal(G, base), (Q, Vr, T)
+            assert np.array_equal(G, base), (Q, Vr, T, co)
 
 
 def test_autograd_backward_is_the_oracle_adjoint():
@@ -167,6 +170,35 @@ def test_reduced_precision_snapshots_error_is_bounded(prec, bound):
     assert max(errs) <= bound
     # the misfit comes from the FP32 forward sweep and is unaffected
     assert np.all(np.abs(J.cpu().numpy() - J_ref) <= J_TOL * J_ref)
+    # the same snapshots with the coefficients in global memory: identical
+    fwi.set_plan(2, 4, 0, g.nsrc, coeff=2)
+    Jg, Gg = fwi.gradient(_t(V), _t(d_obs), sigma, precision=prec)
+    Jg, Gg = Jg.clone(), Gg.clone()
+    fwi.set_plan(2, 4, 0, g.nsrc, coeff=1)
+    Js, Gs = fwi.gradient(_t(V), _t(d_obs), sigma, precision=prec)
+    assert torch.equal(Gg, Gs) and torch.equal(Jg, Js)
+
+
+@pytest.mark.parametrize("K", [1, 9])
+def test_global_coefficients_equal_shared_bit_for_bit(K):
+    """w' and the gradient accumulator in global memory (the layout for
+    large grids) give the same traces, misfits and gradients as the
+    shared-memory layout, with and without restart checkpoints, and the
+    adjoint-only mode agrees too."""
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    Vt, Dt = _t(V), _t(d_obs)
+    fwi.set_mode(vg.FWI_MODE_BATCHED, K)
+    out = {}
+    for co in (1, 2):
+        fwi.set_plan(3, 8, 0, g.nsrc, coeff=co)
+        S = fwi.forward(Vt).clone()
+        J, G = fwi.gradient(Vt, Dt, sigma)
+        J, G = J.clone(), G.clone()
+        A = fwi.adjoint(Vt, S - Dt[None]).clone()
+        out[co] = (S, J, G, A)
+    for a, b in zip(out[1], out[2]):
+        assert torch.equal(a, b)
 
 
 def test_noise_free_data_give_zero_misfit_and_gradient():
