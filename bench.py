@@ -346,6 +346,7 @@ def run_other_workload(args, torch):
     P = args.particles or (40 if args.workload == "ssvgd" else 64)
     geo, fwi, X0, dobs_h, sigma, lo, hi = build_problem(cfg, max(P, 2000) if args.workload == "ssvgd" else P, 0, dev, vg, torch)
     fwi.set_autotune(not args.no_autotune)
+    prec = {"fp32": vg.FWI_FP32, "bf16": vg.FWI_CKPT_BF16, "fp16": vg.FWI_CKPT_FP16}[args.precision]
     dobs = torch.tensor(dobs_h, device=dev)
     lo_t = torch.tensor(lo.reshape(-1), dtype=torch.float32, device=dev)
     hi_t = torch.tensor(hi.reshape(-1), dtype=torch.float32, device=dev)
@@ -360,7 +361,7 @@ def run_other_workload(args, torch):
 
         def step(rec=None):
             sl = X[:P]
-            _, g = fwi.gradient(sl, dobs, sigma)
+            _, g = fwi.gradient(sl, dobs, sigma, precision=prec)
             G[:P].copy_(g.reshape(P, -1))
             if rec: rec[1].record()
             it[0] += 1
@@ -378,7 +379,7 @@ def run_other_workload(args, torch):
             it[0] += 1
             eta = vg.philox_normal(P, d, seed=5, it=it[0], device=dev)
             m = vg.advi_sample(mu, om, eta, a_t, b_t)
-            _, g = fwi.gradient(m, dobs, sigma)
+            _, g = fwi.gradient(m, dobs, sigma, precision=prec)
             if rec: rec[1].record()
             vg.advi_step(mu, om, st, it[0], eta, g.reshape(P, -1), 0.01, a_t, b_t, gscale=-1.0)
     for _ in range(args.warmup):
@@ -401,7 +402,7 @@ def run_other_workload(args, torch):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%s 240x600 grid dx 10 m, 40 src, 400 rec, %d steps dt 0.8 ms, "
                                    "%d gradients per step" % (args.workload, cfg.nt, P),
-                       "plan": fwi.query_plan(P)},
+                       "precision": args.precision, "plan": fwi.query_plan(P, prec)},
             "gcell_updates_per_s": cu * P / (t_fwi * 1e-3) / 1e9,
             "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
             "update": ("ssvgd_step n=2000 d=144000" if args.workload == "ssvgd"
