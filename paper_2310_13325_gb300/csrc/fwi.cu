@@ -112,12 +112,11 @@ static int receiver_pad(int R) { return (R + 3) & ~3; }
 // Shared memory of the batched kernel (floats): two levels, the zero row, w'
 // and (gradient) the accumulator, all [Hb][PX] (w' and the accumulator are
 // left out when they live in global memory, gw); (gz, gz) per row; the
-// column taper; one flag per strip; receiver numbers, cell offsets and two
-// value slots.
+// column taper; receiver numbers, cell offsets and two value slots.
 static size_t wave_smem(int Hb, int V, int PX, int NXg, bool grad, int R, bool gw) {
   const size_t HP = (size_t)Hb * PX;
   size_t f = (gw ? 2 : (grad ? 4 : 3)) * HP + PX + ((2 * Hb + 3) & ~3) + (size_t)NXg * 4 +
-             ((Hb / V + 3) & ~3) + 4 * (size_t)receiver_pad(R);
+             4 * (size_t)receiver_pad(R);
   return f * 4;
 }
 

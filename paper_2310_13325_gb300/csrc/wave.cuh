@@ -236,8 +236,8 @@ __device__ __forceinline__ float2 lap_pair(float2 k1, float2 k2, float2 k3, floa
 // arrays W (w') and Gm (gradient accumulator) all use the row pitch PX, with
 // the cells of a row at columns 4 .. 4+NXg*4-1, so one cell has the same
 // offset in all four; a row of zeros; the row taper as (gz, gz) pairs; the
-// column taper; one flag per strip (taper 1 on all its rows); the band's
-// receiver numbers, cell offsets and two steps of receiver values.
+// column taper; the band's receiver numbers, cell offsets and two steps of
+// receiver values.
 struct Band {
   float *U[2];                 // local field buffers [Hb][PX]
   uint32_t sup[2], sdn[2];     // neighbours' buffers in the cluster window
@@ -247,7 +247,6 @@ struct Band {
   float *Gm;                   // [Hb][PX] gradient accumulator
   float2 *gz2;                 // [Hb] (gz, gz) per row
   float *gxs;                  // [NXg*4]
-  int *sfast;                  // [nstrip] 1 when the taper is 1 on every row of the strip
   int *rid;                    // [Rpad] receiver numbers of this band (rperm order)
   int *roff;                   // [Rpad] their cell offsets in a level buffer
   float *val;                  // [2][Rpad] per-receiver values of two consecutive steps
@@ -322,7 +321,6 @@ struct TaskCtx {
   uint32_t bot, bstr;  // same for row r0+V below the task
   bool tedge, bedge;   // rows above / below come from a neighbour or the zero row
   float2 gxa, gxb;     // column taper of the cell pairs (0,1) and (2,3)
-  bool fast;           // taper 1 on every cell of the task
   bool special;        // forward: holds the source; adjoint: holds receivers
   bool valid;
   int srow, slane;     // source row within the task (-1: none) and lane
@@ -435,18 +433,13 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
     const float2 pa = make_float2(AP.x, AP.y), pb = make_float2(AP.z, AP.w);
     const float2 ta = fma2(wa, s01, add2(c01, c01));
     const float2 tb = fma2(wb, s23, add2(c23, c23));
-    float2 na, nb;
-    if (c.fast) {
-      // taper 1: g [t - g ap] reduces exactly to t - ap
-      na = sub2(ta, pa);
-      nb = sub2(tb, pb);
-    } else {
-      // g [2u + w s - g ap], as update_cell
-      const float2 gz = c.gz[i];
-      const float2 ga = mul2(gz, c.gxa), gb = mul2(gz, c.gxb);
-      na = mul2(ga, fma2(make_float2(-ga.x, -ga.y), pa, ta));
-      nb = mul2(gb, fma2(make_float2(-gb.x, -gb.y), pb, tb));
-    }
+    // g [2u + w s - g ap], as update_cell, on every cell: where the taper is
+    // 1 this is exactly t - ap, and one code path without a per-row branch
+    // runs faster than a separate taper-free path
+    const float2 gz = c.gz[i];
+    const float2 ga = mul2(gz, c.gxa), gb = mul2(gz, c.gxb);
+    const float2 na = mul2(ga, fma2(make_float2(-ga.x, -ga.y), pa, ta));
+    const float2 nb = mul2(gb, fma2(make_float2(-gb.x, -gb.y), pb, tb));
     if (c.valid) st4(rp + dn, make_float4(na.x, na.y, nb.x, nb.y));
     if (SNAP) {
       if (!ADJ) {
@@ -620,7 +613,6 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
     const float4 gx4 = ld4(B.gxs + gcol);
     c.gxa = make_float2(gx4.x, gx4.y);
     c.gxb = make_float2(gx4.z, gx4.w);
-    c.fast = B.sfast[sp] != 0 && gx4.x == 1.f && gx4.y == 1.f && gx4.z == 1.f && gx4.w == 1.f;
     M rm = 0;
     c.rb = 0;
     c.srow = -1;
@@ -717,7 +709,6 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
   const int HP = p.Hb * p.PX;
   const int W4 = p.NXg * 4;
   const int HW = p.Hb * W4;
-  const int nstrip = p.Hb / V;
   Band B;
   B.b = b;
   B.U[0] = smem;
@@ -727,8 +718,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
   B.Gm = GW ? nullptr : B.W + HP;
   B.gz2 = reinterpret_cast<float2 *>(GW ? Zr + p.PX : B.Gm + (MODE != WM_FORWARD ? HP : 0));
   B.gxs = reinterpret_cast<float *>(B.gz2) + ((2 * p.Hb + 3) & ~3);
-  B.sfast = reinterpret_cast<int *>(B.gxs + W4);
-  B.rid = B.sfast + ((nstrip + 3) & ~3);
+  B.rid = reinterpret_cast<int *>(B.gxs + W4);
   B.roff = B.rid + p.Rpad;
   B.val = reinterpret_cast<float *>(B.roff + p.Rpad);
   B.rb0 = p.rbstart[b];
@@ -751,11 +741,6 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
     B.gz2[q] = make_float2(g, g);
   }
   for (int q = tid; q < W4; q += T) B.gxs[q] = p.gx[q];
-  for (int q = tid; q < nstrip; q += T) {
-    int f = 1;
-    for (int r = q * V; r < q * V + V; ++r) f &= p.gz[b * p.Hb + r] == 1.f;
-    B.sfast[q] = f;
-  }
   const size_t slab = (size_t)p.Q * HW;   // elements of one snapshot
 
   for (int item = cid; item < p.items; item += ncl) {
