@@ -1,4 +1,5 @@
-"""FP64 oracle: SVGD (Eq. 13-17) and stochastic SVGD (Eq. 21-25).
+"""FP64 oracle: SVGD (Eq. 13-17) and stochastic SVGD (Eq. 21-25), with the
+RBF kernel or the diagonal matrix-valued kernel of the Discussion.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -102,4 +103,86 @@ def ssvgd_step(X, G, eps, xi, h2=None, lo=None, hi=None):
     phi, h2u, K = svgd_direction(X, G, h2)
     L, tau = jittered_cholesky(K)
     noise = np.sqrt(2.0 * eps / n) * (L @ np.asarray(xi, dtype=np.float64))
+    return clip(X + eps * phi + noise, lo, hi), h2u, tau
+
+
+# ---------------------------------------------------------------------------
+# Diagonal matrix-valued kernel (Discussion of the paper; Wang et al. 2019).
+#
+# With a positive diagonal preconditioner Q = diag(q), the kernel is the
+# matrix K_Q(m', m) = Q^{-1} k_Q(m', m), where k_Q is the RBF kernel in the
+# Q-metric, k_Q(m', m) = exp(-(m' - m)^T Q (m' - m) / (2 h^2)), and h^2 follows
+# the median rule on the Q-weighted squared distances. The SVGD direction
+# (Eq. 17 with this kernel) is
+#   phi(m_i) = 1/n sum_j [K_Q(m_j, m_i) G_j + div_{m_j} K_Q(m_j, m_i)],
+# the divergence taken over the columns of K_Q: for a diagonal constant Q it
+# is Q^{-1} grad_{m_j} k_Q(m_j, m_i). The paper sets q to the inverse of the
+# variance of each coordinate across the particles (population variance
+# here; coordinates with zero variance get q = 1). For sSVGD the diffusion
+# matrix becomes (1/n) Kbar (x) Q^{-1}, whose square root is
+# (1/sqrt(n)) Lk (x) Q^{-1/2}.
+
+def inverse_variance(X):
+    """q [d]: 1 / Var_j(X[j, c]) (population variance over the particles),
+    1 where the variance is zero."""
+    X = np.asarray(X, dtype=np.float64)
+    var = ((X - X.mean(axis=0, keepdims=True)) ** 2).mean(axis=0)
+    q = np.ones_like(var)
+    pos = var > 0
+    q[pos] = 1.0 / var[pos]
+    return q
+
+
+def pairwise_sqdist_q(X, q):
+    """D2[i, j] = sum_c q_c (X[i, c] - X[j, c])^2, taken directly."""
+    X = np.asarray(X, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64).reshape(1, -1)
+    n = X.shape[0]
+    D2 = np.zeros((n, n))
+    for i in range(n):
+        diff = X - X[i][None, :]
+        D2[i] = (q * diff * diff).sum(axis=1)
+    return D2
+
+
+def svgd_direction_q(X, G, q, h2=None):
+    """phi [n, d] with the diagonal matrix-valued kernel, the bandwidth used
+    and the scalar factor k_Q as Kbar."""
+    X = np.asarray(X, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    n = X.shape[0]
+    D2 = pairwise_sqdist_q(X, q)
+    if h2 is None or h2 <= 0:
+        h2 = median_bandwidth(D2)
+    K = rbf(D2, h2)                        # k_Q(m_i, m_j)
+    qinv = 1.0 / q
+    phi = np.zeros_like(X)
+    for i in range(n):
+        for j in range(n):
+            # K_Q(m_j, m_i) G_j = Q^{-1} k_Q G_j
+            drive = qinv * (K[i, j] * G[j])
+            # grad_{m_j} k_Q(m_j, m_i) = k_Q Q (m_i - m_j) / h^2, times Q^{-1}
+            grad_k = K[i, j] * q * (X[i] - X[j]) / h2
+            phi[i] += drive + qinv * grad_k
+    return phi / n, h2, K
+
+
+def svgd_step_q(X, G, q, eps, h2=None, lo=None, hi=None):
+    """One SVGD update with the diagonal matrix-valued kernel, then the bound
+    reset."""
+    phi, h2u, _ = svgd_direction_q(X, G, q, h2)
+    return clip(np.asarray(X, dtype=np.float64) + eps * phi, lo, hi), h2u
+
+
+def ssvgd_step_q(X, G, q, eps, xi, h2=None, lo=None, hi=None):
+    """One stochastic SVGD update with the diagonal matrix-valued kernel:
+    drift phi above, noise sqrt(2 eps / n) (Lk Xi) Q^{-1/2} (column c scaled
+    by 1/sqrt(q_c)). Returns (X_new, h2, tau)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    phi, h2u, K = svgd_direction_q(X, G, q, h2)
+    L, tau = jittered_cholesky(K)
+    noise = np.sqrt(2.0 * eps / n) * (L @ np.asarray(xi, dtype=np.float64))
+    noise = noise / np.sqrt(np.asarray(q, dtype=np.float64))[None, :]
     return clip(X + eps * phi + noise, lo, hi), h2u, tau

@@ -10,6 +10,15 @@
 * sSVGD with n = 1 is the unadjusted Langevin algorithm, whose stationary
   variance on N(mu, s^2) is s^2 / (1 - eps / (2 s^2));
 * sSVGD noise covariance is (2 eps / n) (Kbar + tau I).
+
+Diagonal matrix-valued kernel (Q = diag(q)):
+* q = 1 reduces to the RBF kernel exactly;
+* brute force: phi rebuilt from Q^{-1} k_Q and finite-difference gradients of
+  k_Q (pins the Q^{-1} factor and the Q-metric);
+* change of coordinates: the RBF SVGD / sSVGD of z = sqrt(q) m with
+  gradients G / sqrt(q) and the same noise, mapped back by 1 / sqrt(q);
+* n = 1 is preconditioned gradient ascent, phi = G / q;
+* q from the particles is the inverse population variance.
 """
 import numpy as np
 
@@ -165,3 +174,84 @@ def test_clip_resets_to_nearest_bound():
     X = np.array([[0.5, 3.0, -2.0]])
     out = svgd.clip(X, np.array([0.0, 0.0, -1.0]), np.array([1.0, 2.0, 1.0]))
     assert np.array_equal(out, [[0.5, 2.0, -1.0]])
+
+
+# ---------------------------------------------------------------------------
+# diagonal matrix-valued kernel
+
+def _case_q(n, d, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d)) * rng.uniform(0.2, 5.0, size=(1, d))
+    G = rng.standard_normal((n, d))
+    q = svgd.inverse_variance(X)
+    return X, G, q
+
+
+def test_matrix_kernel_with_unit_q_is_the_rbf_kernel():
+    X, G, _ = _case_q(5, 7, 1)
+    q = np.ones(7)
+    phi_q, h2_q, K_q = svgd.svgd_direction_q(X, G, q)
+    phi, h2, K = svgd.svgd_direction(X, G)
+    assert np.isclose(h2_q, h2, rtol=1e-14)
+    assert np.allclose(phi_q, phi, rtol=1e-13, atol=1e-14)
+    xi = np.random.default_rng(2).standard_normal(X.shape)
+    a = svgd.ssvgd_step_q(X, G, q, 0.01, xi)[0]
+    b = svgd.ssvgd_step(X, G, 0.01, xi)[0]
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-14)
+
+
+def test_matrix_kernel_phi_brute_force_tiny():
+    X, G, q = _case_q(3, 2, 3)
+    phi, h2, _ = svgd.svgd_direction_q(X, G, q)
+    n, d = X.shape
+
+    def kq(a, b):
+        return np.exp(-np.sum(q * (a - b) ** 2) / (2 * h2))
+
+    ref = np.zeros_like(X)
+    e = 1e-6
+    for i in range(n):
+        for j in range(n):
+            grad = np.zeros(d)
+            for c in range(d):
+                dp = X[j].copy(); dp[c] += e
+                dm = X[j].copy(); dm[c] -= e
+                grad[c] = (kq(dp, X[i]) - kq(dm, X[i])) / (2 * e)
+            # K_Q = Q^{-1} k_Q; its divergence in m_j is Q^{-1} grad k_Q
+            ref[i] += (kq(X[j], X[i]) * G[j] + grad) / q
+    ref /= n
+    assert np.allclose(phi, ref, rtol=1e-7, atol=1e-9)
+
+
+def test_matrix_kernel_is_rbf_svgd_in_scaled_coordinates():
+    X, G, q = _case_q(6, 5, 4)
+    s = np.sqrt(q)[None, :]
+    phi_q, h2_q, _ = svgd.svgd_direction_q(X, G, q)
+    phi_z, h2_z, _ = svgd.svgd_direction(X * s, G / s)
+    assert np.isclose(h2_q, h2_z, rtol=1e-12)
+    assert np.allclose(phi_q, phi_z / s, rtol=1e-10, atol=1e-12)
+    xi = np.random.default_rng(5).standard_normal(X.shape)
+    eps = 0.03
+    Xq = svgd.ssvgd_step_q(X, G, q, eps, xi)[0]
+    Zn = svgd.ssvgd_step(X * s, G / s, eps, xi)[0]
+    assert np.allclose(Xq, Zn / s, rtol=1e-10, atol=1e-12)
+
+
+def test_matrix_kernel_single_particle_is_preconditioned_ascent():
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((1, 4))
+    G = rng.standard_normal((1, 4))
+    q = np.array([0.5, 2.0, 4.0, 10.0])
+    phi, _, _ = svgd.svgd_direction_q(X, G, q)
+    assert np.allclose(phi, G / q, rtol=1e-14)
+
+
+def test_inverse_variance_is_population_variance():
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((9, 6)) * 3.0
+    X[:, 2] = 1.5                              # zero variance -> q = 1
+    q = svgd.inverse_variance(X)
+    var = np.var(X, axis=0)                    # numpy: population variance
+    assert q[2] == 1.0
+    m = np.arange(6) != 2
+    assert np.allclose(q[m], 1.0 / var[m], rtol=1e-13)
