@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--config", default="cfg3")
     ap.add_argument("--particles", type=int, default=0)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--svgd-kernel", default="rbf", choices=["rbf", "diag"],
+                    help="RBF kernel, or the diagonal matrix-valued kernel with Q the "
+                         "inverse particle variance")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -168,6 +171,8 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     ws = torch.empty(vg.svgd_workspace_size(P, cfg.d, gram, False), dtype=torch.uint8,
                      device=dev)
     h2 = torch.empty(1, dtype=torch.float64, device=dev)
+    qv = torch.empty(cfg.d, dtype=torch.float32, device=dev)
+    diag = args.svgd_kernel == "diag"
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
     eps_box = {}
@@ -178,8 +183,12 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
             # step size: the first update moves the fastest coordinate ~20 m/s
             g = grad.abs().max().item()
             eps_box["eps"] = 20.0 / max(g, 1e-30)
+        svgd_update()
+
+    def svgd_update():
+        q = vg.svgd_inverse_variance(X, out=qv) if diag else None
         vg.svgd_step(X, grad.reshape(P, -1), eps_box["eps"], lo=lo_t, hi=hi_t,
-                     gram_precision=gram, ws=ws, h2_used=h2, gscale=-1.0)
+                     gram_precision=gram, ws=ws, h2_used=h2, gscale=-1.0, q=q)
 
     # warm-up (includes the autotuner's timed trials on the first call)
     for _ in range(args.warmup):
@@ -202,8 +211,7 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
         e0.record(stream)
         fwi.gradient(X, dobs, sigma, precision=prec, misfit=misfit, grad=grad)
         e1.record(stream)
-        vg.svgd_step(X, grad.reshape(P, -1), eps_box["eps"], lo=lo_t, hi=hi_t,
-                     gram_precision=gram, ws=ws, h2_used=h2, gscale=-1.0)
+        svgd_update()
         e2.record(stream)
     torch.cuda.synchronize()
     if ws_ > 1:
@@ -365,7 +373,9 @@ def run_other_workload(args, torch):
             G[:P].copy_(g.reshape(P, -1))
             if rec: rec[1].record()
             it[0] += 1
-            vg.ssvgd_step(X, G, 1e-3, seed=3, it=it[0], lo=lo_t, hi=hi_t, ws=ws, gscale=-1.0)
+            q = vg.svgd_inverse_variance(X) if args.svgd_kernel == "diag" else None
+            vg.ssvgd_step(X, G, 1e-3, seed=3, it=it[0], lo=lo_t, hi=hi_t, ws=ws, gscale=-1.0,
+                          q=q)
     else:
         d = cfg.d
         mu = torch.tensor(((lo + hi) / 2).reshape(-1), dtype=torch.float32, device=dev)
@@ -405,8 +415,8 @@ def run_other_workload(args, torch):
                        "precision": args.precision, "plan": fwi.query_plan(P, prec)},
             "gcell_updates_per_s": cu * P / (t_fwi * 1e-3) / 1e9,
             "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
-            "update": ("ssvgd_step n=2000 d=144000" if args.workload == "ssvgd"
-                       else "advi_step S=64 d=144000")}
+            "update": ("ssvgd_step n=2000 d=144000, %s kernel" % args.svgd_kernel
+                       if args.workload == "ssvgd" else "advi_step S=64 d=144000")}
     if args.workload == "ssvgd":
         line["iteration_s_for_2000_particles"] = (2000.0 / P) * t_fwi * 1e-3 + t_upd * 1e-3
     print(json.dumps(line))
@@ -472,6 +482,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(cfg, P), "precision": args.precision,
+                   "svgd_kernel": args.svgd_kernel,
                    "l2": "flushed between timed steps (256 MB write)",
                    "plan": res["plan"]},
         "gcell_updates_per_s": cu * units / (t_max * 1e-3) / 1e9,
@@ -490,7 +501,7 @@ def main():
                      "note": "algorithmic 16 B per cell update; the fields stay in shared "
                              "memory, DRAM sees the stored snapshots only (traffic, "
                              "dram_gbs: ncu bytes per launch scaled by cell updates)"},
-        "gpu_launches": (2 + 24) * args.steps,
+        "gpu_launches": (2 + 24 + (args.svgd_kernel == "diag")) * args.steps,
         "clocks": res["clocks"],
     }
     if e2e_max:

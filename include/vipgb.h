@@ -260,6 +260,33 @@ int  ssvgd_step(float *X, const float *G, float gscale, int n, int d, float eps,
                 uint64_t seed, uint64_t iter, const float *xi,
                 double *tau_used, vip_stream_t stream);
 
+/* SVGD and sSVGD with the diagonal matrix-valued kernel (Discussion
+ * section; Wang et al. 2019): K_Q(m', m) = Q^{-1} k_Q(m', m), Q = diag(q),
+ * k_Q(m', m) = exp(-(m' - m)^T Q (m' - m) / (2 h^2)), h^2 by the median rule
+ * on the Q-weighted squared distances. The direction is
+ *   phi(m_i) = 1/n sum_j k_Q(m_j, m_i) [G_j / q + (m_i - m_j) / h^2]
+ * and the sSVGD noise sqrt(2 eps / n) (Lk Xi) Q^{-1/2}. q: device [d],
+ * positive (typically 1 / the variance of each coordinate across the
+ * particles, svgd_inverse_variance). All other arguments, the workspace
+ * size and the errors are those of svgd_step / ssvgd_step; q = NULL is
+ * VIP_ERR_ARG. With q = 1 the results equal svgd_step / ssvgd_step bit for
+ * bit. */
+int  svgd_step_q(float *X, const float *G, float gscale, const float *q, int n,
+                 int d, float eps, float h2, const float *lo, const float *hi,
+                 int gram_precision, void *ws, size_t ws_bytes, double *h2_used,
+                 vip_stream_t stream);
+int  ssvgd_step_q(float *X, const float *G, float gscale, const float *q, int n,
+                  int d, float eps, float h2, const float *lo, const float *hi,
+                  int gram_precision, void *ws, size_t ws_bytes,
+                  double *h2_used, uint64_t seed, uint64_t iter,
+                  const float *xi, double *tau_used, vip_stream_t stream);
+
+/* q_c = 1 / Var_j(X[j][c]) for the particles X [n][d] (device, FP32 in,
+ * FP64 two-pass population variance), 1 where the variance is zero; the
+ * choice of Q the Discussion section gives. q: device [d], caller-owned. */
+int  svgd_inverse_variance(const float *X, int n, int d, float *q,
+                           vip_stream_t stream);
+
 /* ======================================================================
  * Mean-field ADVI (Eq. 7-12 with a diagonal Cholesky factor, Sec. 5):
  * theta = mu + e^omega * eta, m = T^{-1}(theta) with the logit transform of

@@ -24,7 +24,7 @@ FWI_FP32, FWI_CKPT_BF16, FWI_CKPT_FP16 = 0, 1, 2
 FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
 VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
 
-__all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "advi_sample", "advi_step",
+__all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "svgd_inverse_variance", "advi_sample", "advi_step",
            "philox_normal", "svgd_workspace_size", "svgd_sqdist", "svgd_step_noalloc", "FWI_FP32", "FWI_CKPT_BF16",
            "FWI_CKPT_FP16", "FWI_MODE_BATCHED", "FWI_MODE_PLAIN", "VIP_GRAM_BF16",
            "VIP_GRAM_BF16X3", "VIP_GRAM_FP32", "VipError"]
@@ -240,20 +240,41 @@ def svgd_sqdist(X, gram_precision=VIP_GRAM_BF16X3, ws=None, stream=None):
 
 
 def svgd_step(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GRAM_BF16X3,
-              ws=None, h2_used=None, gscale=1.0, stream=None):
-    """In-place SVGD update of X [n, d] (Eq. 17) with grad log p = gscale * G.
-    Returns the workspace tensor (reusable) and h2_used (device float64 [1])."""
+              ws=None, h2_used=None, gscale=1.0, q=None, stream=None):
+    """In-place SVGD update of X [n, d] (Eq. 17) with grad log p = gscale * G;
+    with q (device [d]) the diagonal matrix-valued kernel Q = diag(q)
+    (svgd_step_q). Returns the workspace tensor (reusable) and h2_used
+    (device float64 [1])."""
     torch = _torch()
     n, d = X.shape
     ws = _workspace(n, d, gram_precision, False, ws, X.device)
     if h2_used is None:
         h2_used = torch.empty(1, dtype=torch.float64, device=X.device)
-    check(_lib.load().svgd_step(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
-                                float(gscale), n, d, float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
-                                _ptr(hi, torch.float32, "hi"), int(gram_precision),
-                                _ptr(ws), ws.numel(), _ptr(h2_used, torch.float64),
-                                _stream(stream)), "svgd_step")
+    common = (n, d, float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
+              _ptr(hi, torch.float32, "hi"), int(gram_precision), _ptr(ws), ws.numel(),
+              _ptr(h2_used, torch.float64), _stream(stream))
+    if q is None:
+        check(_lib.load().svgd_step(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
+                                    float(gscale), *common), "svgd_step")
+    else:
+        check(_lib.load().svgd_step_q(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
+                                      float(gscale), _ptr(q, torch.float32, "q"), *common),
+              "svgd_step_q")
     return ws, h2_used
+
+
+def svgd_inverse_variance(X, out=None, stream=None):
+    """q [d] = 1 / variance of each coordinate across the particles X [n, d]
+    (population variance; 1 where it is zero), the Q of the matrix-valued
+    kernel."""
+    torch = _torch()
+    n, d = X.shape
+    if out is None:
+        out = torch.empty(d, dtype=torch.float32, device=X.device)
+    check(_lib.load().svgd_inverse_variance(_ptr(X, torch.float32, "X"), n, d,
+                                            _ptr(out, torch.float32, "q"), _stream(stream)),
+          "svgd_inverse_variance")
+    return out
 
 
 def svgd_step_noalloc(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GRAM_BF16X3,
@@ -274,9 +295,10 @@ def svgd_step_noalloc(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GR
 
 def ssvgd_step(X, G, eps, seed, it, xi=None, h2=0.0, lo=None, hi=None,
                gram_precision=VIP_GRAM_BF16X3, ws=None, h2_used=None, tau_used=None,
-               gscale=1.0, stream=None):
+               gscale=1.0, q=None, stream=None):
     """In-place stochastic SVGD update of X [n, d] (Eq. 22 with the noise of
-    Eq. 25); xi None draws the noise from Philox(seed, it) on the device."""
+    Eq. 25); xi None draws the noise from Philox(seed, it) on the device; q
+    (device [d]) selects the diagonal matrix-valued kernel (ssvgd_step_q)."""
     torch = _torch()
     n, d = X.shape
     ws = _workspace(n, d, gram_precision, True, ws, X.device)
@@ -284,13 +306,17 @@ def ssvgd_step(X, G, eps, seed, it, xi=None, h2=0.0, lo=None, hi=None,
         h2_used = torch.empty(1, dtype=torch.float64, device=X.device)
     if tau_used is None:
         tau_used = torch.empty(1, dtype=torch.float64, device=X.device)
-    check(_lib.load().ssvgd_step(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
-                                 float(gscale), n, d, float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
-                                 _ptr(hi, torch.float32, "hi"), int(gram_precision),
-                                 _ptr(ws), ws.numel(), _ptr(h2_used, torch.float64),
-                                 int(seed), int(it), _ptr(xi, torch.float32, "xi"),
-                                 _ptr(tau_used, torch.float64), _stream(stream)),
-          "ssvgd_step")
+    common = (n, d, float(eps), float(h2), _ptr(lo, torch.float32, "lo"),
+              _ptr(hi, torch.float32, "hi"), int(gram_precision), _ptr(ws), ws.numel(),
+              _ptr(h2_used, torch.float64), int(seed), int(it), _ptr(xi, torch.float32, "xi"),
+              _ptr(tau_used, torch.float64), _stream(stream))
+    if q is None:
+        check(_lib.load().ssvgd_step(_ptr(X, torch.float32, "X"), _ptr(G, torch.float32, "G"),
+                                     float(gscale), *common), "ssvgd_step")
+    else:
+        check(_lib.load().ssvgd_step_q(_ptr(X, torch.float32, "X"),
+                                       _ptr(G, torch.float32, "G"), float(gscale),
+                                       _ptr(q, torch.float32, "q"), *common), "ssvgd_step_q")
     return ws, h2_used, tau_used
 
 

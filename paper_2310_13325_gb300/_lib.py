@@ -50,6 +50,13 @@ _SIGS = {
     "ssvgd_step": (c_int, [c_void_p, c_void_p, c_float, c_int, c_int, c_float, c_float, c_void_p,
                            c_void_p, c_int, c_void_p, c_size_t, c_void_p, c_uint64,
                            c_uint64, c_void_p, c_void_p, c_void_p]),
+    "svgd_step_q": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_int, c_int, c_float,
+                            c_float, c_void_p, c_void_p, c_int, c_void_p, c_size_t, c_void_p,
+                            c_void_p]),
+    "ssvgd_step_q": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_int, c_int, c_float,
+                             c_float, c_void_p, c_void_p, c_int, c_void_p, c_size_t, c_void_p,
+                             c_uint64, c_uint64, c_void_p, c_void_p, c_void_p]),
+    "svgd_inverse_variance": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "advi_sample": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
                             c_void_p, c_void_p, c_void_p]),
     "advi_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_float,

@@ -19,6 +19,12 @@
 // The repulsive term uses the identity sum_j k_ij (m_i - m_j) =
 // r_i xc_i - (Kbar Xc)_i, exact in real arithmetic because the particle
 // mean cancels; centring keeps it well conditioned in FP32.
+//
+// Diagonal matrix-valued kernel K_Q = Q^{-1} k_Q, Q = diag(q) (Discussion
+// section): step 1 stores the centred particles scaled by sqrt(q), so steps
+// 2-6 see the Q-metric; the update divides the driving term K G by q and the
+// repulsive term and the sSVGD noise by sqrt(q), column by column (the
+// repulsion is formed from the scaled Xc, whose factor sqrt(q) it removes).
 #include "common.cuh"
 #include "gram.cuh"
 #include "philox.cuh"
@@ -83,9 +89,9 @@ static size_t layout(int n, int d, int gp, int stochastic, void *base, size_t ca
 }
 
 // ---------------------------------------------------------------------------
-__global__ void centre_kernel(const float *__restrict__ X, int n, int d, int dp, int np,
-                              double *mean, float *Xc, __nv_bfloat16 *Xh, __nv_bfloat16 *Xm,
-                              __nv_bfloat16 *Xl) {
+__global__ void centre_kernel(const float *__restrict__ X, const float *__restrict__ q, int n,
+                              int d, int dp, int np, double *mean, float *Xc, __nv_bfloat16 *Xh,
+                              __nv_bfloat16 *Xm, __nv_bfloat16 *Xl) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= dp) return;
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
@@ -100,8 +106,10 @@ __global__ void centre_kernel(const float *__restrict__ X, int n, int d, int dp,
   for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * d + c];
   const double m = s / n;
   mean[c] = m;
+  const double sq = q ? sqrt((double)q[c]) : 1.0;   // Q-metric scale of the column
   for (int i = 0; i < n; ++i) {
-    const float xc = (float)((double)X[(size_t)i * d + c] - m);
+    const float xc = q ? (float)(((double)X[(size_t)i * d + c] - m) * sq)
+                       : (float)((double)X[(size_t)i * d + c] - m);
     Xc[(size_t)i * d + c] = xc;
     if (Xh) {
       // three-piece BF16 split: each remainder is exact in FP32
@@ -120,6 +128,23 @@ __global__ void centre_kernel(const float *__restrict__ X, int n, int d, int dp,
       Xh[(size_t)i * dp + c] = z;
       if (Xm) { Xm[(size_t)i * dp + c] = z; Xl[(size_t)i * dp + c] = z; }
     }
+}
+
+// q_c = 1 / Var_j(x_jc), the population variance over the particles in
+// FP64 (two passes), and 1 where the variance is zero.
+__global__ void inverse_variance_kernel(const float *__restrict__ X, int n, int d, float *q) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * d + c];
+  const double m = s / n;
+  double v = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double t = (double)X[(size_t)i * d + c] - m;
+    v += t * t;
+  }
+  v /= n;
+  q[c] = v > 0.0 ? (float)(1.0 / v) : 1.f;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -405,7 +430,7 @@ __global__ void __launch_bounds__(256) update_kernel(
     const float *__restrict__ K, const float *__restrict__ G, const float *__restrict__ Xc,
     const float *__restrict__ Lk, const float *__restrict__ Xi, const float *__restrict__ rs,
     const double *h2p, int n, int d, float eps, float gscale, float noise_scale,
-    const float *lo, const float *hi, float *X) {
+    const float *__restrict__ q, const float *lo, const float *hi, float *X) {
   constexpr int BK = 16;
   __shared__ float Ks[BK][64], Ls[NOISE ? BK : 1][64];
   __shared__ __align__(16) float Gs[BK][64], Xs[BK][64], Es[NOISE ? BK : 1][64];
@@ -460,10 +485,22 @@ __global__ void __launch_bounds__(256) update_kernel(
       const int c = c0 + tx * 4 + v;
       if (c >= d) continue;
       const size_t g = (size_t)i * d + c;
-      const float rep = (fmaf(ri, Xc[g], -a2[u][v])) * inv_h2;
-      const float phi = fmaf(gscale, a1[u][v], rep) * inv_n;
-      float x = fmaf(eps, phi, X[g]);
-      if (NOISE) x = fmaf(noise_scale, a3[u][v], x);
+      float x;
+      if (!q) {
+        const float rep = (fmaf(ri, Xc[g], -a2[u][v])) * inv_h2;
+        const float phi = fmaf(gscale, a1[u][v], rep) * inv_n;
+        x = fmaf(eps, phi, X[g]);
+        if (NOISE) x = fmaf(noise_scale, a3[u][v], x);
+      } else {
+        // matrix-valued kernel: Q^{-1} on the driving term, Q^{-1/2} on the
+        // repulsion (built from sqrt(q)-scaled Xc) and on the noise
+        const double qc = (double)q[c];
+        const float iq = (float)(1.0 / qc), isq = (float)(1.0 / sqrt(qc));
+        const float rep = (fmaf(ri, Xc[g], -a2[u][v])) * inv_h2 * isq;
+        const float phi = fmaf(gscale * iq, a1[u][v], rep) * inv_n;
+        x = fmaf(eps, phi, X[g]);
+        if (NOISE) x = fmaf(noise_scale * isq, a3[u][v], x);
+      }
       if (lo) x = fmaxf(x, lo[c]);
       if (hi) x = fminf(x, hi[c]);
       X[g] = x;
@@ -472,11 +509,11 @@ __global__ void __launch_bounds__(256) update_kernel(
 }
 
 // Steps 1-5: centring, Gram, FP64 distances and the bandwidth.
-static int distances(const float *X, int n, int d, float h2, int gp, SvgdWs &w,
+static int distances(const float *X, const float *q, int n, int d, float h2, int gp, SvgdWs &w,
                      double *h2_used, cudaStream_t st) {
   const bool tc = gp != VIP_GRAM_FP32;
   const bool x3 = gp == VIP_GRAM_BF16X3;
-  centre_kernel<<<idiv_up(w.dp, 128), 128, 0, st>>>(X, n, d, w.dp, w.np, w.mean, w.Xc,
+  centre_kernel<<<idiv_up(w.dp, 128), 128, 0, st>>>(X, q, n, d, w.dp, w.np, w.mean, w.Xc,
                                                     tc ? w.Xh : nullptr, x3 ? w.Xm : nullptr,
                                                     x3 ? w.Xl : nullptr);
   VIP_CHECK_LAUNCH();
@@ -521,23 +558,22 @@ static int check_args(const float *X, int n, int d, int gp, void *ws) {
   return VIP_OK;
 }
 
-static int run_svgd(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
-                    const float *lo,
-                    const float *hi, int gp, void *ws, size_t ws_bytes, double *h2_used,
-                    bool stochastic, uint64_t seed, uint64_t it, const float *xi,
-                    double *tau_used, cudaStream_t st) {
+static int run_svgd(float *X, const float *G, float gscale, const float *q, int n, int d,
+                    float eps, float h2, const float *lo, const float *hi, int gp, void *ws,
+                    size_t ws_bytes, double *h2_used, bool stochastic, uint64_t seed,
+                    uint64_t it, const float *xi, double *tau_used, cudaStream_t st) {
   if (check_args(X, n, d, gp, ws) || !G || !(eps >= 0.f)) return VIP_ERR_ARG;
   SvgdWs w;
   const size_t need = layout(n, d, gp, stochastic, ws, ws_bytes, w);
   if (need > ws_bytes) return VIP_ERR_NOMEM;
-  int rc = distances(X, n, d, h2, gp, w, h2_used, st);
+  int rc = distances(X, q, n, d, h2, gp, w, h2_used, st);
   if (rc) return rc;
   kbar_kernel<<<n, 256, 0, st>>>(w.D2, n, w.h2, w.K, w.rs);
   VIP_CHECK_LAUNCH();
   const dim3 ug(idiv_up(d, 64), idiv_up(n, 64));
   if (!stochastic) {
     update_kernel<false><<<ug, 256, 0, st>>>(w.K, G, w.Xc, nullptr, nullptr, w.rs, w.h2, n, d,
-                                             eps, gscale, 0.f, lo, hi, X);
+                                             eps, gscale, 0.f, q, lo, hi, X);
     VIP_CHECK_LAUNCH();
     return VIP_OK;
   }
@@ -581,7 +617,7 @@ static int run_svgd(float *X, const float *G, float gscale, int n, int d, float 
   }
   const float ns = (float)std::sqrt(2.0 * (double)eps / n);
   update_kernel<true><<<ug, 256, 0, st>>>(w.K, G, w.Xc, w.Lk, noise, w.rs, w.h2, n, d, eps, gscale,
-                                          ns, lo, hi, X);
+                                          ns, q, lo, hi, X);
   VIP_CHECK_LAUNCH();
   // tau is a host local: make the asynchronous copy complete before return
   if (tau_used) VIP_TRY(cudaStreamSynchronize(st));
@@ -634,8 +670,8 @@ int svgd_step_noalloc(float *X, const float *G, float gscale, int n, int d, floa
   void *ws = nullptr;
   int rc = noalloc_scratch(&ws);
   if (rc) return rc;
-  return run_svgd(X, G, gscale, n, d, eps, h2, lo, hi, gram_precision, ws, kNoallocScratchBytes,
-                  h2_used, false, 0, 0, nullptr, nullptr, stream);
+  return run_svgd(X, G, gscale, nullptr, n, d, eps, h2, lo, hi, gram_precision, ws,
+                  kNoallocScratchBytes, h2_used, false, 0, 0, nullptr, nullptr, stream);
 }
 
 size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic) {
@@ -647,16 +683,40 @@ size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic) {
 int svgd_step(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
               const float *lo, const float *hi, int gram_precision, void *ws, size_t ws_bytes,
               double *h2_used, vip_stream_t stream) {
-  return run_svgd(X, G, gscale, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes, h2_used, false, 0,
-                  0, nullptr, nullptr, stream);
+  return run_svgd(X, G, gscale, nullptr, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes,
+                  h2_used, false, 0, 0, nullptr, nullptr, stream);
 }
 
 int ssvgd_step(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
                const float *lo, const float *hi, int gram_precision, void *ws, size_t ws_bytes,
                double *h2_used, uint64_t seed, uint64_t iter, const float *xi,
                double *tau_used, vip_stream_t stream) {
-  return run_svgd(X, G, gscale, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes, h2_used, true, seed,
-                  iter, xi, tau_used, stream);
+  return run_svgd(X, G, gscale, nullptr, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes,
+                  h2_used, true, seed, iter, xi, tau_used, stream);
+}
+
+int svgd_step_q(float *X, const float *G, float gscale, const float *q, int n, int d, float eps,
+                float h2, const float *lo, const float *hi, int gram_precision, void *ws,
+                size_t ws_bytes, double *h2_used, vip_stream_t stream) {
+  if (!q) return VIP_ERR_ARG;
+  return run_svgd(X, G, gscale, q, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes, h2_used,
+                  false, 0, 0, nullptr, nullptr, stream);
+}
+
+int ssvgd_step_q(float *X, const float *G, float gscale, const float *q, int n, int d, float eps,
+                 float h2, const float *lo, const float *hi, int gram_precision, void *ws,
+                 size_t ws_bytes, double *h2_used, uint64_t seed, uint64_t iter, const float *xi,
+                 double *tau_used, vip_stream_t stream) {
+  if (!q) return VIP_ERR_ARG;
+  return run_svgd(X, G, gscale, q, n, d, eps, h2, lo, hi, gram_precision, ws, ws_bytes, h2_used,
+                  true, seed, iter, xi, tau_used, stream);
+}
+
+int svgd_inverse_variance(const float *X, int n, int d, float *q, vip_stream_t stream) {
+  if (!X || !q || n < 1 || d < 1) return VIP_ERR_ARG;
+  inverse_variance_kernel<<<idiv_up(d, 128), 128, 0, stream>>>(X, n, d, q);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
 }
 
 int svgd_sqdist(const float *X, int n, int d, int gram_precision, double *D2,
@@ -664,7 +724,7 @@ int svgd_sqdist(const float *X, int n, int d, int gram_precision, double *D2,
   if (check_args(X, n, d, gram_precision, ws) || !D2) return VIP_ERR_ARG;
   SvgdWs w;
   if (layout(n, d, gram_precision, 0, ws, ws_bytes, w) > ws_bytes) return VIP_ERR_NOMEM;
-  int rc = distances(X, n, d, 0.f, gram_precision, w, h2_used, stream);
+  int rc = distances(X, nullptr, n, d, 0.f, gram_precision, w, h2_used, stream);
   if (rc) return rc;
   const size_t nn = (size_t)n * n;
   copy_d2_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(w.D2, nn, D2);

@@ -195,3 +195,75 @@ def test_advi_sample_and_step_match_oracle(bounded):
         mur, omr, ref_state = oadvi.advi_step(mur, omr, ref_state, t, eta, gm, 0.01, a, b)
     assert rel(mut.cpu().numpy(), mur) <= 1e-5
     assert rel(omt.cpu().numpy(), omr) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# diagonal matrix-valued kernel (svgd_step_q, ssvgd_step_q, svgd_inverse_variance)
+
+def _scaled_case(n, d, seed):
+    """Particles whose coordinates have spreads from 0.1 to 20, so that the
+    inverse-variance metric differs strongly from the Euclidean one."""
+    rng = np.random.default_rng(seed)
+    scale = rng.uniform(0.1, 20.0, size=(1, d))
+    X = (rng.standard_normal((n, d)) * scale).astype(np.float32).astype(np.float64)
+    G = (rng.standard_normal((n, d)) / scale).astype(np.float32).astype(np.float64)
+    return X, G
+
+
+@pytest.mark.parametrize("n,d", [(9, 4096), (2, 3), (130, 1000)])
+def test_inverse_variance_matches_oracle(n, d):
+    X, _ = _scaled_case(n, d, seed=n)
+    X[:, 0] = X[0, 0]                     # a coordinate without spread: q = 1
+    q = vg.svgd_inverse_variance(_t(X)).cpu().numpy()
+    ref = osvgd.inverse_variance(X)
+    assert q[0] == 1.0
+    assert np.allclose(q, ref, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("gp", EXACT_GRAMS)
+@pytest.mark.parametrize("n,d", [(8, 4096), (3, 2), (130, 1000)])
+def test_matrix_kernel_svgd_step_matches_oracle(gp, n, d):
+    X, G = _scaled_case(n, d, seed=n + 2 * d)
+    Xt = _t(X)
+    q = vg.svgd_inverse_variance(Xt)
+    qh = q.double().cpu().numpy()         # the same q on both sides
+    phi0, _, _ = osvgd.svgd_direction_q(X, G, qh)
+    eps = 0.5 / np.abs(phi0 / X.std(axis=0, keepdims=True).clip(1e-30)).max()
+    ws, h2 = vg.svgd_step(Xt, _t(G), eps, gram_precision=gp, q=q)
+    X_ref, h2_ref = osvgd.svgd_step_q(X, G, qh, eps)
+    phi = (Xt.double().cpu().numpy() - X) / eps
+    phi_ref = (X_ref - X) / eps
+    assert rel(phi, phi_ref) <= 1e-5, rel(phi, phi_ref)
+    # the Gram is accumulated in FP32: centred particles are strongly
+    # anticorrelated at small n (G_ij ~ -|x|^2 / (n - 1)), and d/16 sequential
+    # FP32 additions of partial sums of that size bound the relative error of
+    # the median distance by 2 (d/16) 2^-24 |G| / med ~ 2e-6 for n = 8,
+    # d = 4096 (measured 1.3e-6); 1e-5 is the FP32 bound used for phi
+    assert abs(h2.item() - h2_ref) <= 1e-5 * h2_ref
+
+
+def test_matrix_kernel_with_unit_q_equals_rbf_bit_for_bit():
+    X, G = _unit_case(40, 2000, seed=21)
+    xi = _t(np.random.default_rng(22).standard_normal(X.shape))
+    ones = torch.ones(X.shape[1], device=DEV)
+    A, B = _t(X), _t(X)
+    vg.svgd_step(A, _t(G), 0.1)
+    vg.svgd_step(B, _t(G), 0.1, q=ones)
+    assert torch.equal(A, B)
+    A, B = _t(X), _t(X)
+    vg.ssvgd_step(A, _t(G), 0.05, seed=0, it=0, xi=xi)
+    vg.ssvgd_step(B, _t(G), 0.05, seed=0, it=0, xi=xi, q=ones)
+    assert torch.equal(A, B)
+
+
+def test_matrix_kernel_ssvgd_step_injected_noise_matches_oracle():
+    X, G = _scaled_case(16, 3000, seed=23)
+    xi = np.random.default_rng(24).standard_normal(X.shape).astype(np.float32).astype(np.float64)
+    Xt = _t(X)
+    q = vg.svgd_inverse_variance(Xt)
+    qh = q.double().cpu().numpy()
+    eps = 0.05
+    ws, h2, tau = vg.ssvgd_step(Xt, _t(G), eps, seed=0, it=0, xi=_t(xi), q=q)
+    X_ref, h2_ref, tau_ref = osvgd.ssvgd_step_q(X, G, qh, eps, xi)
+    assert tau.item() == pytest.approx(tau_ref)
+    assert rel(Xt.cpu().numpy() - X, X_ref - X) <= 1e-5
