@@ -305,6 +305,19 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
       }
     }
   }
+  // the global-coefficient layout is for grids whose shared-memory bands
+  // leave SMs idle; when a shared-memory plan already occupies 80 % of the
+  // SMs it only adds L2 traffic, so it is not offered (unless forced)
+  if (c->force_coeff != 2) {
+    bool full = false;
+    for (auto &p : out) full |= !p.gw && (double)p.maxcl * p.Q >= 0.8 * c->sm_count;
+    if (full) {
+      std::vector<Plan> keep;
+      for (auto &p : out)
+        if (!p.gw) keep.push_back(p);
+      out.swap(keep);
+    }
+  }
   return out.empty() ? VIP_ERR_UNSUPPORTED : VIP_OK;
 }
 
