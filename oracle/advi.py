@@ -1,4 +1,5 @@
-"""FP64 oracle: mean-field ADVI (Eq. 7-12) with Adam ascent.
+"""FP64 oracle: mean-field ADVI (Eq. 7-12) with Adam ascent (and the SGD,
+ADAGRAD and ADADELTA rules the paper also lists).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -73,3 +74,62 @@ def advi_step(mu, omega, state, t, eta, gm, lr, a=None, b=None):
     mu, m_mu, v_mu = adam_ascent(mu, gmu, m_mu, v_mu, t, lr)
     omega, m_om, v_om = adam_ascent(omega, gom, m_om, v_om, t, lr)
     return mu, omega, (m_mu, v_mu, m_om, v_om)
+
+
+# ---------------------------------------------------------------------------
+# The other ascent rules of Sec. 5 (the paper lists SGD, ADAGRAD, ADADELTA and
+# ADAM for the ELBO), written from their published definitions (Duchi et al.
+# 2011, diagonal form; Zeiler 2012), each increasing the objective:
+#   SGD       p <- p + lr g
+#   ADAGRAD   G <- G + g^2;  p <- p + lr g / (sqrt(G) + eps)            eps 1e-8
+#   ADADELTA  E[g^2] <- rho E[g^2] + (1 - rho) g^2
+#             dx = sqrt(E[dx^2] + eps) / sqrt(E[g^2] + eps) g
+#             E[dx^2] <- rho E[dx^2] + (1 - rho) dx^2;  p <- p + lr dx  rho 0.95, eps 1e-6
+#                                                                     (lr = 1 is Zeiler's rule)
+#   ADAM      adam_ascent above
+# Each keeps two state arrays per variable (s1, s2): unused (SGD), (G, -)
+# (ADAGRAD), (E[g^2], E[dx^2]) (ADADELTA), (m, v) (ADAM).
+
+SGD, ADAGRAD, ADADELTA, ADAM = 0, 1, 2, 3
+ADAGRAD_EPS = 1e-8
+ADADELTA_RHO, ADADELTA_EPS = 0.95, 1e-6
+
+
+def sgd_ascent(p, grad, lr):
+    return p + lr * grad
+
+
+def adagrad_ascent(p, grad, acc, lr):
+    acc = acc + grad * grad
+    return p + lr * grad / (np.sqrt(acc) + ADAGRAD_EPS), acc
+
+
+def adadelta_ascent(p, grad, eg2, edx2, lr):
+    eg2 = ADADELTA_RHO * eg2 + (1.0 - ADADELTA_RHO) * grad * grad
+    dx = np.sqrt(edx2 + ADADELTA_EPS) / np.sqrt(eg2 + ADADELTA_EPS) * grad
+    edx2 = ADADELTA_RHO * edx2 + (1.0 - ADADELTA_RHO) * dx * dx
+    return p + lr * dx, eg2, edx2
+
+
+def ascend(p, grad, s1, s2, t, lr, opt):
+    """One step of the chosen rule; returns (p, s1, s2)."""
+    if opt == SGD:
+        return sgd_ascent(p, grad, lr), s1, s2
+    if opt == ADAGRAD:
+        p, s1 = adagrad_ascent(p, grad, s1, lr)
+        return p, s1, s2
+    if opt == ADADELTA:
+        return adadelta_ascent(p, grad, s1, s2, lr)
+    if opt == ADAM:
+        return adam_ascent(p, grad, s1, s2, t, lr)
+    raise ValueError("unknown optimizer %r" % (opt,))
+
+
+def advi_step_opt(mu, omega, state, t, eta, gm, lr, opt, a=None, b=None):
+    """advi_step with the ascent rule opt (SGD, ADAGRAD, ADADELTA, ADAM);
+    state = (s1_mu, s2_mu, s1_omega, s2_omega)."""
+    gmu, gom = elbo_gradients(mu, omega, eta, gm, a, b)
+    s1m, s2m, s1o, s2o = state
+    mu, s1m, s2m = ascend(mu, gmu, s1m, s2m, t, lr, opt)
+    omega, s1o, s2o = ascend(omega, gom, s1o, s2o, t, lr, opt)
+    return mu, omega, (s1m, s2m, s1o, s2o)

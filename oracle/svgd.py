@@ -186,3 +186,41 @@ def ssvgd_step_q(X, G, q, eps, xi, h2=None, lo=None, hi=None):
     noise = np.sqrt(2.0 * eps / n) * (L @ np.asarray(xi, dtype=np.float64))
     noise = noise / np.sqrt(np.asarray(q, dtype=np.float64))[None, :]
     return clip(X + eps * phi + noise, lo, hi), h2u, tau
+
+
+# ---------------------------------------------------------------------------
+# SVGD / sSVGD in the unconstrained space (Sec. 3, second strategy for the
+# uniform prior): the particles are theta = T(m) with the logit transform of
+# Eq. (12), T(m) = log(m - a) - log(b - m), m = T^{-1}(theta) =
+# a + (b - a) / (1 + e^{-theta}), and the target is the density of theta,
+# p(m(theta)) |dm/dtheta|. Its gradient, by the chain rule and the derivative
+# of the log-Jacobian log((b - a) s (1 - s)), s = sigmoid(theta), is
+#   grad_theta = grad_m log p * (b - a) s (1 - s) + (1 - 2 s).
+# The update runs on theta without a bound reset.
+
+def to_unconstrained(m, a, b):
+    m = np.asarray(m, dtype=np.float64)
+    return np.log(m - a) - np.log(b - m)
+
+
+def to_model(theta, a, b):
+    theta = np.asarray(theta, dtype=np.float64)
+    return a + (b - a) / (1.0 + np.exp(-theta))
+
+
+def unconstrained_gradient(theta, gm, a, b):
+    """grad_theta log p_theta from gm = grad_m log p at m = T^{-1}(theta)."""
+    s = 1.0 / (1.0 + np.exp(-np.asarray(theta, dtype=np.float64)))
+    return np.asarray(gm, dtype=np.float64) * (b - a) * s * (1.0 - s) + (1.0 - 2.0 * s)
+
+
+def svgd_step_unconstrained(theta, gm, eps, a, b, h2=None):
+    """One SVGD update of theta (Eq. 17) for the transformed target."""
+    g = unconstrained_gradient(theta, gm, a, b)
+    return svgd_step(theta, g, eps, h2)
+
+
+def ssvgd_step_unconstrained(theta, gm, eps, xi, a, b, h2=None):
+    """One sSVGD update of theta (Eq. 22, 25) for the transformed target."""
+    g = unconstrained_gradient(theta, gm, a, b)
+    return ssvgd_step(theta, g, eps, xi, h2)

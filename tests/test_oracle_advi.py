@@ -5,7 +5,10 @@
 * one step: the Monte-Carlo ELBO gradients equal central differences of the
   ELBO estimator at fixed eta (Eq. 10-11 restricted to the diagonal);
 * optimum: on a linear-Gaussian target the mean-field optimum is
-  mu = posterior mean, sigma_i = 1 / sqrt(Lambda_ii) (closed form).
+  mu = posterior mean, sigma_i = 1 / sqrt(Lambda_ii) (closed form), reached
+  by each ascent rule (SGD, ADAGRAD, ADADELTA, ADAM);
+* first steps in closed form: ADAGRAD moves by lr sign(g); ADADELTA by
+  sqrt(eps) g / sqrt((1 - rho) g^2 + eps); SGD by lr g.
 """
 import numpy as np
 
@@ -100,3 +103,37 @@ def test_meanfield_optimum_linear_gaussian():
         mu, om, st = advi.advi_step(mu, om, st, t, eta, gm, lr)
     assert np.allclose(mu, mu_t, atol=0.02)
     assert np.allclose(np.exp(om), 1 / np.sqrt(np.diag(Lam)), rtol=0.03)
+
+
+def test_first_steps_of_the_ascent_rules():
+    g = np.array([2.0, -0.5, 1e-3])
+    z = np.zeros(3)
+    p, s1, s2 = advi.ascend(z, g, z, z, 1, 0.1, advi.SGD)
+    assert np.allclose(p, 0.1 * g, rtol=1e-15)
+    p, s1, s2 = advi.ascend(z, g, z, z, 1, 0.1, advi.ADAGRAD)
+    assert np.allclose(p, 0.1 * np.sign(g), rtol=1e-4)
+    assert np.allclose(s1, g * g, rtol=1e-15)
+    p, s1, s2 = advi.ascend(z, g, z, z, 1, 1.0, advi.ADADELTA)
+    rho, e = advi.ADADELTA_RHO, advi.ADADELTA_EPS
+    dx = np.sqrt(e) * g / np.sqrt((1 - rho) * g * g + e)
+    assert np.allclose(p, dx, rtol=1e-13)
+    assert np.allclose(s2, (1 - rho) * dx * dx, rtol=1e-13)
+
+
+def test_every_ascent_rule_reaches_the_meanfield_optimum():
+    d = 3
+    mu_t, Lam = _gauss_target(d, 5)
+    rates = {advi.SGD: (0.05, 0.005), advi.ADAGRAD: (0.5, 0.05),
+             advi.ADADELTA: (1.0, 0.2), advi.ADAM: (0.05, 0.005)}
+    for opt, (lr0, lr1) in rates.items():
+        rng = np.random.default_rng(7)
+        mu = np.zeros(d)
+        om = np.zeros(d)
+        st = tuple(np.zeros(d) for _ in range(4))
+        for t in range(1, 3001):
+            eta = rng.standard_normal((64, d))
+            m = advi.sample(mu, om, eta)
+            gm = -(m - mu_t[None, :]) @ Lam.T
+            mu, om, st = advi.advi_step_opt(mu, om, st, t, eta, gm, lr0 if t < 2000 else lr1, opt)
+        assert np.allclose(mu, mu_t, atol=0.02), opt
+        assert np.allclose(np.exp(om), 1 / np.sqrt(np.diag(Lam)), rtol=0.03), opt

@@ -19,6 +19,13 @@ Diagonal matrix-valued kernel (Q = diag(q)):
   gradients G / sqrt(q) and the same noise, mapped back by 1 / sqrt(q);
 * n = 1 is preconditioned gradient ascent, phi = G / q;
 * q from the particles is the inverse population variance.
+
+Unconstrained (logit) space:
+* T and T^{-1} invert each other; the transformed gradient equals central
+  differences of log p(T^{-1}(theta)) + log|dT^{-1}/dtheta| for a Gaussian
+  log p in m;
+* one particle on a uniform target ascends the logistic density of theta to
+  its mode theta = 0 (the middle of the box).
 """
 import numpy as np
 
@@ -255,3 +262,42 @@ def test_inverse_variance_is_population_variance():
     assert q[2] == 1.0
     m = np.arange(6) != 2
     assert np.allclose(q[m], 1.0 / var[m], rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# unconstrained (logit) space
+
+def test_unconstrained_transform_and_gradient():
+    rng = np.random.default_rng(8)
+    d = 5
+    a = rng.uniform(1000, 2000, d)
+    b = a + rng.uniform(500, 3000, d)
+    m = a + (b - a) * rng.uniform(0.05, 0.95, d)
+    th = svgd.to_unconstrained(m, a, b)
+    assert np.allclose(svgd.to_model(th, a, b), m, rtol=1e-13)
+    c = a + 0.3 * (b - a)
+    s2 = ((b - a) / 4) ** 2
+
+    def logp_theta(t):
+        mm = a + (b - a) / (1.0 + np.exp(-t))
+        # log p(m) + log|dm/dtheta|, the Jacobian from central differences of m(theta)
+        e = 1e-6
+        dm = ((a + (b - a) / (1.0 + np.exp(-(t + e)))) - (a + (b - a) / (1.0 + np.exp(-(t - e))))) / (2 * e)
+        return np.sum(-0.5 * (mm - c) ** 2 / s2) + np.sum(np.log(dm))
+
+    gm = -(m - c) / s2
+    g = svgd.unconstrained_gradient(th, gm, a, b)
+    e = 1e-4
+    fd = np.array([(logp_theta(th + e * np.eye(d)[k]) - logp_theta(th - e * np.eye(d)[k])) / (2 * e)
+                   for k in range(d)])
+    assert np.allclose(g, fd, rtol=1e-5, atol=1e-6)
+
+
+def test_unconstrained_single_particle_uniform_target_reaches_mode():
+    a = np.array([1500.0, 2000.0])
+    b = np.array([3000.0, 2600.0])
+    th = np.array([[2.5, -3.0]])
+    for _ in range(400):
+        th, _ = svgd.svgd_step_unconstrained(th, np.zeros_like(th), 0.5, a, b)
+    assert np.allclose(th, 0.0, atol=1e-8)
+    assert np.allclose(svgd.to_model(th, a, b), (a + b) / 2, rtol=1e-10)
