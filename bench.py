@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--svgd-kernel", default="rbf", choices=["rbf", "diag"],
                     help="RBF kernel, or the diagonal matrix-valued kernel with Q the "
                          "inverse particle variance")
+    ap.add_argument("--svgd-space", default="model", choices=["model", "unconstrained"],
+                    help="update the particles with the bound reset, or in the logit-"
+                         "transformed space")
+    ap.add_argument("--advi-rule", default="adam", choices=["sgd", "adagrad", "adadelta", "adam"],
+                    help="ascent rule of the ADVI workload")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -185,10 +190,28 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
             eps_box["eps"] = 20.0 / max(g, 1e-30)
         svgd_update()
 
+    uncon = args.svgd_space == "unconstrained"
+    if uncon:
+        # the transform is undefined on the bounds themselves: prior draws that
+        # rounded onto a bound in FP32 start just inside it
+        pad = 1e-4 * (hi_t - lo_t)
+        X.copy_(torch.minimum(torch.maximum(X, lo_t + pad), hi_t - pad))
+    theta = vg.to_unconstrained(X, lo_t, hi_t) if uncon else None
+    gth = torch.empty_like(X) if uncon else None
+
     def svgd_update():
-        q = vg.svgd_inverse_variance(X, out=qv) if diag else None
-        vg.svgd_step(X, grad.reshape(P, -1), eps_box["eps"], lo=lo_t, hi=hi_t,
-                     gram_precision=gram, ws=ws, h2_used=h2, gscale=-1.0, q=q)
+        if not uncon:
+            q = vg.svgd_inverse_variance(X, out=qv) if diag else None
+            vg.svgd_step(X, grad.reshape(P, -1), eps_box["eps"], lo=lo_t, hi=hi_t,
+                         gram_precision=gram, ws=ws, h2_used=h2, gscale=-1.0, q=q)
+            return
+        # strategy 2 of the uniform prior: the particles live in theta = T(m)
+        vg.unconstrained_gradient(theta, grad.reshape(P, -1), lo_t, hi_t, gscale=-1.0, out=gth)
+        if "eps_t" not in eps_box:
+            eps_box["eps_t"] = 0.1 / max(gth.abs().max().item(), 1e-30)
+        q = vg.svgd_inverse_variance(theta, out=qv) if diag else None
+        vg.svgd_step(theta, gth, eps_box["eps_t"], gram_precision=gram, ws=ws, h2_used=h2, q=q)
+        vg.to_model(theta, lo_t, hi_t, out=X)
 
     # warm-up (includes the autotuner's timed trials on the first call)
     for _ in range(args.warmup):
@@ -391,7 +414,11 @@ def run_other_workload(args, torch):
             m = vg.advi_sample(mu, om, eta, a_t, b_t)
             _, g = fwi.gradient(m, dobs, sigma, precision=prec)
             if rec: rec[1].record()
-            vg.advi_step(mu, om, st, it[0], eta, g.reshape(P, -1), 0.01, a_t, b_t, gscale=-1.0)
+            rule = {"sgd": vg.ASCENT_SGD, "adagrad": vg.ASCENT_ADAGRAD,
+                    "adadelta": vg.ASCENT_ADADELTA, "adam": vg.ASCENT_ADAM}[args.advi_rule]
+            lr = 1.0 if rule == vg.ASCENT_ADADELTA else 0.01
+            vg.advi_step_opt(mu, om, st, it[0], eta, g.reshape(P, -1), lr, rule, a_t, b_t,
+                             gscale=-1.0)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -416,7 +443,8 @@ def run_other_workload(args, torch):
             "gcell_updates_per_s": cu * P / (t_fwi * 1e-3) / 1e9,
             "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
             "update": ("ssvgd_step n=2000 d=144000, %s kernel" % args.svgd_kernel
-                       if args.workload == "ssvgd" else "advi_step S=64 d=144000")}
+                       if args.workload == "ssvgd"
+                       else "advi_step S=64 d=144000, %s" % args.advi_rule)}
     if args.workload == "ssvgd":
         line["iteration_s_for_2000_particles"] = (2000.0 / P) * t_fwi * 1e-3 + t_upd * 1e-3
     print(json.dumps(line))
@@ -482,7 +510,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(cfg, P), "precision": args.precision,
-                   "svgd_kernel": args.svgd_kernel,
+                   "svgd_kernel": args.svgd_kernel, "svgd_space": args.svgd_space,
                    "l2": "flushed between timed steps (256 MB write)",
                    "plan": res["plan"]},
         "gcell_updates_per_s": cu * units / (t_max * 1e-3) / 1e9,
@@ -501,7 +529,8 @@ def main():
                      "note": "algorithmic 16 B per cell update; the fields stay in shared "
                              "memory, DRAM sees the stored snapshots only (traffic, "
                              "dram_gbs: ncu bytes per launch scaled by cell updates)"},
-        "gpu_launches": (2 + 24 + (args.svgd_kernel == "diag")) * args.steps,
+        "gpu_launches": (2 + 24 + (args.svgd_kernel == "diag") +
+                         2 * (args.svgd_space == "unconstrained")) * args.steps,
         "clocks": res["clocks"],
     }
     if e2e_max:

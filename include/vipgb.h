@@ -311,6 +311,40 @@ int  advi_step(float *mu, float *omega, float *adam_state, int t,
                const float *a, const float *b, float lr,
                vip_stream_t stream);
 
+/* advi_step with a choice of ascent rule among those the paper lists for the
+ * ELBO (Sec. 5): VIP_ASCENT_SGD (p += lr g), VIP_ASCENT_ADAGRAD (Duchi et al.
+ * 2011, diagonal: G += g^2, p += lr g / (sqrt(G) + 1e-8)), VIP_ASCENT_ADADELTA
+ * (Zeiler 2012, rho 0.95, eps 1e-6; lr multiplies the step, 1 is Zeiler's
+ * rule) and VIP_ASCENT_ADAM (exactly advi_step). state: device [4][d],
+ * zero before the first step: two values per variable, (s1_mu, s2_mu,
+ * s1_omega, s2_omega); unused by SGD. Errors: VIP_ERR_ARG for an unknown
+ * rule, otherwise as advi_step. */
+#define VIP_ASCENT_SGD      0
+#define VIP_ASCENT_ADAGRAD  1
+#define VIP_ASCENT_ADADELTA 2
+#define VIP_ASCENT_ADAM     3
+int  advi_step_opt(float *mu, float *omega, float *state, int t,
+                   const float *eta, const float *gm, float gscale, int S, int d,
+                   const float *a, const float *b, float lr, int rule,
+                   vip_stream_t stream);
+
+/* SVGD / sSVGD in the unconstrained space (Sec. 3, second strategy for the
+ * uniform prior): particles theta = T(m) with the transform of Eq. (12),
+ * T(m) = log(m - a) - log(b - m), T^{-1}(theta) = a + (b - a) / (1 + e^-theta),
+ * updated by svgd_step / ssvgd_step (without bounds) with the gradient of
+ * the transformed density,
+ *   g_theta = gscale gm (b - a) s (1 - s) + (1 - 2 s),  s = sigmoid(theta),
+ * gm = grad_m of the log-likelihood (or log posterior) at m = T^{-1}(theta).
+ * All arrays device [n][d] (a, b: [d]); elementwise, in place allowed for
+ * the transforms. Errors: VIP_ERR_ARG for NULL pointers or n, d < 1. */
+int  vip_to_unconstrained(const float *m, const float *a, const float *b, int n,
+                          int d, float *theta, vip_stream_t stream);
+int  vip_to_model(const float *theta, const float *a, const float *b, int n,
+                  int d, float *m, vip_stream_t stream);
+int  vip_unconstrained_gradient(const float *theta, const float *gm, float gscale,
+                                const float *a, const float *b, int n, int d,
+                                float *g, vip_stream_t stream);
+
 /* Standard normals out[rows][cols] from the Philox-4x32-10 stream used by
  * ssvgd_step (same counter layout), for the ADVI draws eta. */
 int  vip_philox_normal(float *out, int rows, int cols, uint64_t seed,

@@ -24,7 +24,9 @@ FWI_FP32, FWI_CKPT_BF16, FWI_CKPT_FP16 = 0, 1, 2
 FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
 VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
 
-__all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "svgd_inverse_variance", "advi_sample", "advi_step",
+__all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "svgd_inverse_variance",
+           "advi_step_opt", "to_unconstrained", "to_model", "unconstrained_gradient",
+           "ASCENT_SGD", "ASCENT_ADAGRAD", "ASCENT_ADADELTA", "ASCENT_ADAM", "advi_sample", "advi_step",
            "philox_normal", "svgd_workspace_size", "svgd_sqdist", "svgd_step_noalloc", "FWI_FP32", "FWI_CKPT_BF16",
            "FWI_CKPT_FP16", "FWI_MODE_BATCHED", "FWI_MODE_PLAIN", "VIP_GRAM_BF16",
            "VIP_GRAM_BF16X3", "VIP_GRAM_FP32", "VipError"]
@@ -345,6 +347,63 @@ def advi_step(mu, omega, adam_state, t, eta, gm, lr, a=None, b=None, gscale=1.0,
                                 _ptr(eta, torch.float32, "eta"), _ptr(gm, torch.float32, "gm"),
                                 float(gscale), S, d, _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
                                 float(lr), _stream(stream)), "advi_step")
+
+
+ASCENT_SGD, ASCENT_ADAGRAD, ASCENT_ADADELTA, ASCENT_ADAM = 0, 1, 2, 3
+
+
+def advi_step_opt(mu, omega, state, t, eta, gm, lr, rule, a=None, b=None, gscale=1.0,
+                  stream=None):
+    """advi_step with the ascent rule ASCENT_SGD, ASCENT_ADAGRAD,
+    ASCENT_ADADELTA or ASCENT_ADAM; state [4, d] zero-initialised."""
+    torch = _torch()
+    S, d = eta.shape
+    check(_lib.load().advi_step_opt(_ptr(mu, torch.float32, "mu"),
+                                    _ptr(omega, torch.float32, "omega"),
+                                    _ptr(state, torch.float32, "state"), int(t),
+                                    _ptr(eta, torch.float32, "eta"),
+                                    _ptr(gm, torch.float32, "gm"), float(gscale), S, d,
+                                    _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                    float(lr), int(rule), _stream(stream)), "advi_step_opt")
+
+
+def to_unconstrained(m, a, b, out=None, stream=None):
+    """theta = log(m - a) - log(b - m) (Eq. 12), m [n, d], a, b [d]."""
+    torch = _torch()
+    n, d = m.shape
+    out = torch.empty_like(m) if out is None else out
+    check(_lib.load().vip_to_unconstrained(_ptr(m, torch.float32, "m"), _ptr(a, torch.float32, "a"),
+                                           _ptr(b, torch.float32, "b"), n, d,
+                                           _ptr(out, torch.float32, "theta"), _stream(stream)),
+          "vip_to_unconstrained")
+    return out
+
+
+def to_model(theta, a, b, out=None, stream=None):
+    """m = a + (b - a) / (1 + e^-theta) (Eq. 12)."""
+    torch = _torch()
+    n, d = theta.shape
+    out = torch.empty_like(theta) if out is None else out
+    check(_lib.load().vip_to_model(_ptr(theta, torch.float32, "theta"),
+                                   _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                   n, d, _ptr(out, torch.float32, "m"), _stream(stream)),
+          "vip_to_model")
+    return out
+
+
+def unconstrained_gradient(theta, gm, a, b, gscale=1.0, out=None, stream=None):
+    """Gradient of the transformed log-density for theta from gscale * gm,
+    the gradient in the model space at m = T^{-1}(theta)."""
+    torch = _torch()
+    n, d = theta.shape
+    out = torch.empty_like(theta) if out is None else out
+    check(_lib.load().vip_unconstrained_gradient(_ptr(theta, torch.float32, "theta"),
+                                                 _ptr(gm, torch.float32, "gm"), float(gscale),
+                                                 _ptr(a, torch.float32, "a"),
+                                                 _ptr(b, torch.float32, "b"), n, d,
+                                                 _ptr(out, torch.float32, "g"), _stream(stream)),
+          "vip_unconstrained_gradient")
+    return out
 
 
 def philox_normal(rows, cols, seed, it, out=None, device="cuda"):

@@ -267,3 +267,89 @@ def test_matrix_kernel_ssvgd_step_injected_noise_matches_oracle():
     X_ref, h2_ref, tau_ref = osvgd.ssvgd_step_q(X, G, qh, eps, xi)
     assert tau.item() == pytest.approx(tau_ref)
     assert rel(Xt.cpu().numpy() - X, X_ref - X) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# ADVI ascent rules (advi_step_opt) and SVGD in the unconstrained space
+
+def _advi_case(d, S, seed, bounded):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(1500, 2000, d) if bounded else None
+    b = a + rng.uniform(500, 1500, d) if bounded else None
+    mu = rng.standard_normal(d) * 0.5
+    om = rng.standard_normal(d) * 0.2 - 1.0
+    eta = rng.standard_normal((S, d))
+    gm = rng.standard_normal((S, d)) * 1e-3
+    f32 = lambda x: None if x is None else x.astype(np.float32).astype(np.float64)
+    return tuple(map(f32, (mu, om, eta, gm, a, b)))
+
+
+@pytest.mark.parametrize("rule", [vg.ASCENT_SGD, vg.ASCENT_ADAGRAD, vg.ASCENT_ADADELTA,
+                                  vg.ASCENT_ADAM])
+def test_advi_ascent_rules_match_oracle(rule):
+    d, S = 5000, 64
+    mu, om, eta, gm, a, b = _advi_case(d, S, 31, True)
+    lr = {vg.ASCENT_SGD: 0.5, vg.ASCENT_ADAGRAD: 0.01, vg.ASCENT_ADADELTA: 1.0,
+          vg.ASCENT_ADAM: 0.01}[rule]
+    st = torch.zeros((4, d), device=DEV)
+    mut, omt = _t(mu), _t(om)
+    state = tuple(np.zeros(d) for _ in range(4))
+    mur, omr = mu.copy(), om.copy()
+    for t in (1, 2, 3):
+        vg.advi_step_opt(mut, omt, st, t, _t(eta), _t(gm), lr, rule, _t(a), _t(b))
+        mur, omr, state = oadvi.advi_step_opt(mur, omr, state, t, eta, gm, lr, rule, a, b)
+    # compare the moves (the particles' own FP32 rounding would mask them)
+    assert rel(mut.double().cpu().numpy() - mu, mur - mu) <= 1e-5, rule
+    assert rel(omt.double().cpu().numpy() - om, omr - om) <= 1e-5, rule
+
+
+def test_advi_step_opt_adam_is_advi_step():
+    d, S = 3000, 16
+    mu, om, eta, gm, a, b = _advi_case(d, S, 32, True)
+    st1, st2 = torch.zeros((4, d), device=DEV), torch.zeros((4, d), device=DEV)
+    m1, o1, m2, o2 = _t(mu), _t(om), _t(mu), _t(om)
+    for t in (1, 2):
+        vg.advi_step(m1, o1, st1, t, _t(eta), _t(gm), 0.02, _t(a), _t(b))
+        vg.advi_step_opt(m2, o2, st2, t, _t(eta), _t(gm), 0.02, vg.ASCENT_ADAM, _t(a), _t(b))
+    assert torch.equal(m1, m2) and torch.equal(o1, o2) and torch.equal(st1, st2)
+
+
+def test_unconstrained_transforms_match_oracle():
+    rng = np.random.default_rng(33)
+    n, d = 7, 3001
+    a = rng.uniform(1500, 2000, d).astype(np.float32).astype(np.float64)
+    b = (a + rng.uniform(500, 1500, d)).astype(np.float32).astype(np.float64)
+    m = (a + (b - a) * rng.uniform(0.02, 0.98, (n, d))).astype(np.float32).astype(np.float64)
+    gm = (rng.standard_normal((n, d)) * 1e-3).astype(np.float32).astype(np.float64)
+    th = vg.to_unconstrained(_t(m), _t(a), _t(b))
+    th_ref = osvgd.to_unconstrained(m, a, b)
+    assert np.abs(th.cpu().numpy() - th_ref).max() <= 1e-5 * np.abs(th_ref).max()
+    thh = th.double().cpu().numpy()
+    m2 = vg.to_model(th, _t(a), _t(b))
+    assert rel(m2.cpu().numpy(), osvgd.to_model(thh, a, b)) <= 1e-6
+    g = vg.unconstrained_gradient(th, _t(gm), _t(a), _t(b), gscale=-1.0)
+    assert rel(g.cpu().numpy(), osvgd.unconstrained_gradient(thh, -gm, a, b)) <= 1e-5
+
+
+@pytest.mark.parametrize("stochastic", [False, True])
+def test_svgd_in_unconstrained_space_matches_oracle(stochastic):
+    """One update of theta = T(m) with the transformed gradient (strategy 2 of
+    the uniform prior): vip_unconstrained_gradient then svgd_step /
+    ssvgd_step without bounds, against the oracle."""
+    rng = np.random.default_rng(34)
+    n, d = 24, 2000
+    a = rng.uniform(1500, 2000, d).astype(np.float32).astype(np.float64)
+    b = (a + rng.uniform(500, 1500, d)).astype(np.float32).astype(np.float64)
+    th = (rng.standard_normal((n, d)) * 1.5).astype(np.float32).astype(np.float64)
+    gm = (rng.standard_normal((n, d)) * 1e-2).astype(np.float32).astype(np.float64)
+    tht = _t(th)
+    g = vg.unconstrained_gradient(tht, _t(gm), _t(a), _t(b))
+    eps = 0.05
+    if not stochastic:
+        vg.svgd_step(tht, g, eps)
+        ref, _ = osvgd.svgd_step_unconstrained(th, gm, eps, a, b)
+    else:
+        xi = rng.standard_normal((n, d)).astype(np.float32).astype(np.float64)
+        vg.ssvgd_step(tht, g, eps, seed=0, it=0, xi=_t(xi))
+        ref, _, _ = osvgd.ssvgd_step_unconstrained(th, gm, eps, xi, a, b)
+    assert rel(tht.double().cpu().numpy() - th, ref - th) <= 1e-5
