@@ -238,14 +238,17 @@ def pair_gradient(v, geom, isrc, resid_fn, both_forms=False):
     return traces, grad
 
 
-def gradient(v, geom, d_obs, sigma):
-    """Misfit J and dJ/dv [nz, nx] for one model, summed over all sources.
+def gradient(v, geom, d_obs, sigma, sources=None):
+    """Misfit J and dJ/dv [nz, nx] for one model, summed over all sources, or
+    over the listed sources only (a minibatch of the data, Sec. 3 after
+    Eq. 22: (S / len(sources)) times the sum is an unbiased estimate of the
+    full values when the minibatch is drawn uniformly).
 
     d_obs [S, R, nt] observed traces, sigma scalar noise standard deviation."""
     v = np.asarray(v, dtype=np.float64).reshape(geom.nz, geom.nx)
     J = 0.0
     grad = np.zeros((geom.nz, geom.nx))
-    for s in range(geom.nsrc):
+    for s in (range(geom.nsrc) if sources is None else sources):
         def resid_fn(tr, s=s):
             return (tr - d_obs[s]) / sigma ** 2
         tr, gs = pair_gradient(v, geom, s, resid_fn)
@@ -254,13 +257,13 @@ def gradient(v, geom, d_obs, sigma):
     return J, grad
 
 
-def gradients(V, geom, d_obs, sigma):
+def gradients(V, geom, d_obs, sigma, sources=None):
     """Batch version: J [P] and dJ/dv [P, nz*nx]."""
     V = np.asarray(V, dtype=np.float64).reshape(-1, geom.nz, geom.nx)
     J = np.zeros(V.shape[0])
     G = np.zeros((V.shape[0], geom.nz * geom.nx))
     for p in range(V.shape[0]):
-        J[p], g = gradient(V[p], geom, d_obs, sigma)
+        J[p], g = gradient(V[p], geom, d_obs, sigma, sources)
         G[p] = g.reshape(-1)
     return J, G
 

@@ -185,3 +185,27 @@ def test_taper_and_stencil_constants():
     lap8 = fwi.laplacian(x ** 8, 10.0)
     assert np.allclose(lap8[4:-4, 4:-4], 56.0 * x[4:-4, 4:-4] ** 6,
                        rtol=1e-10, atol=1e-3)
+
+
+def test_source_minibatch_sums_and_unbiased_scaling():
+    """The minibatch gradient is the sum over its sources: a partition of the
+    sources adds up to the full misfit and gradient, and (S / nb) times the
+    minibatch value averaged over every subset of nb sources is the full
+    value (the unbiased stochastic gradient of Sec. 3)."""
+    import itertools
+    g = _small_geom(nsrc=4, nt=120)
+    v_true = _small_model(g.nz, g.nx)
+    d_obs = fwi.seismograms(v_true[None], g)[0]
+    v = v_true + 30.0
+    J, G = fwi.gradient(v, g, d_obs, 1.0)
+    Ja, Ga = fwi.gradient(v, g, d_obs, 1.0, sources=[0, 3])
+    Jb, Gb = fwi.gradient(v, g, d_obs, 1.0, sources=[2, 1])
+    assert np.isclose(Ja + Jb, J, rtol=1e-12)
+    assert np.allclose(Ga + Gb, G, rtol=1e-10, atol=1e-12 * np.abs(G).max())
+    nb = 2
+    subsets = list(itertools.combinations(range(4), nb))
+    per = {s: fwi.gradient(v, g, d_obs, 1.0, sources=[s]) for s in range(4)}
+    Jm = np.mean([(4 / nb) * sum(per[s][0] for s in B) for B in subsets])
+    Gm = np.mean([(4 / nb) * sum(per[s][1] for s in B) for B in subsets], axis=0)
+    assert np.isclose(Jm, J, rtol=1e-12)
+    assert np.allclose(Gm, G, rtol=1e-10, atol=1e-12 * np.abs(G).max())
