@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--svgd-space", default="model", choices=["model", "unconstrained"],
                     help="update the particles with the bound reset, or in the logit-"
                          "transformed space")
+    ap.add_argument("--minibatch", type=int, default=0,
+                    help="ssvgd workload: gradients from this many uniformly drawn "
+                         "sources per step (0 = all), scaled by S / minibatch")
     ap.add_argument("--advi-rule", default="adam", choices=["sgd", "adagrad", "adadelta", "adam"],
                     help="ascent rule of the ADVI workload")
     ap.add_argument("--no-plain", action="store_true")
@@ -390,15 +393,21 @@ def run_other_workload(args, torch):
                          dtype=torch.uint8, device=dev)
         it = [0]
 
+        nbatch = min(args.minibatch, cfg.nsrc) if args.minibatch else cfg.nsrc
+        draw = np.random.default_rng(11)
+
         def step(rec=None):
             sl = X[:P]
-            _, g = fwi.gradient(sl, dobs, sigma, precision=prec)
+            srcs = (np.sort(draw.choice(cfg.nsrc, nbatch, replace=False))
+                    if nbatch < cfg.nsrc else None)
+            _, g = fwi.gradient(sl, dobs, sigma, precision=prec, sources=srcs)
             G[:P].copy_(g.reshape(P, -1))
             if rec: rec[1].record()
             it[0] += 1
             q = vg.svgd_inverse_variance(X) if args.svgd_kernel == "diag" else None
-            vg.ssvgd_step(X, G, 1e-3, seed=3, it=it[0], lo=lo_t, hi=hi_t, ws=ws, gscale=-1.0,
-                          q=q)
+            # the minibatch sum times S / nb estimates the full-data gradient
+            vg.ssvgd_step(X, G, 1e-3, seed=3, it=it[0], lo=lo_t, hi=hi_t, ws=ws,
+                          gscale=-cfg.nsrc / nbatch, q=q)
     else:
         d = cfg.d
         mu = torch.tensor(((lo + hi) / 2).reshape(-1), dtype=torch.float32, device=dev)
@@ -433,13 +442,18 @@ def run_other_workload(args, torch):
     t_fwi = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
     t_upd = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
     cu = cell_updates_per_particle(cfg)
+    nsrc_used = cfg.nsrc
+    if args.workload == "ssvgd" and args.minibatch:
+        nsrc_used = min(args.minibatch, cfg.nsrc)
+        cu = cu * nsrc_used / cfg.nsrc      # a minibatch gradient covers nsrc_used sources
     line = {"metric": "FWI particle-gradients/s (%s step, 240x600 shape)" % args.workload,
             "value": P / (t_fwi * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%s 240x600 grid dx 10 m, 40 src, 400 rec, %d steps dt 0.8 ms, "
                                    "%d gradients per step" % (args.workload, cfg.nt, P),
-                       "precision": args.precision, "plan": fwi.query_plan(P, prec)},
+                       "precision": args.precision, "sources_per_gradient": nsrc_used,
+                       "plan": fwi.query_plan(P, prec)},
             "gcell_updates_per_s": cu * P / (t_fwi * 1e-3) / 1e9,
             "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
             "update": ("ssvgd_step n=2000 d=144000, %s kernel" % args.svgd_kernel

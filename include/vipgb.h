@@ -117,7 +117,7 @@ int  fwi_set_mode(fwi_ctx *ctx, int mode, int ckpt_every);
 
 /* Autotuning of the batched launch (cluster size, rows per thread, threads
  * per block). When enabled, the first batched call with a new (P, mode,
- * precision) times short runs (48 steps, one wave of clusters) of the
+ * precision, number of sources) times short runs (48 steps, one wave of clusters) of the
  * candidate launches on the caller's own inputs, synchronously, and caches
  * the fastest in the context; later calls reuse it. Without tuning a cost
  * model picks the launch. fwi_autotune(ctx, P, precision) enables tuning. */
@@ -165,6 +165,18 @@ int  fwi_forward(fwi_ctx *ctx, const float *v, int P, float *seis,
 int  fwi_gradient(fwi_ctx *ctx, const float *v, int P, const float *dobs,
                   double sigma, double *misfit, float *grad, int precision,
                   vip_stream_t stream);
+
+/* fwi_gradient over a minibatch of the sources (the stochastic gradients of
+ * sSVGD from uniformly drawn data subsets, Sec. 3 after Eq. 22): misfit and
+ * gradient are the sums over the nb sources listed in sources (host array of
+ * distinct indices in [0, S)), so (S / nb) times them is an unbiased estimate
+ * of the full-data values (pass that factor as gscale to ssvgd_step). The
+ * listed sources' traces are gathered from dobs [S][R][nt] into context
+ * memory in stream order before the launch. Batched mode only
+ * (VIP_ERR_UNSUPPORTED in plain mode); other errors as fwi_gradient. */
+int  fwi_gradient_sources(fwi_ctx *ctx, const float *v, int P, const float *dobs,
+                          double sigma, const int *sources, int nb, double *misfit,
+                          float *grad, int precision, vip_stream_t stream);
 
 /* Backward of the seismogram map (the autograd rule of fwi_forward):
  *   dseis [P][S][R][nt] upstream sensitivity dL/dseis

@@ -149,8 +149,10 @@ class Fwi:
         return out
 
     def gradient(self, v, dobs, sigma, precision=FWI_FP32, misfit=None, grad=None,
-                 stream=None):
-        """Returns (misfit [P] float64, dJ/dv [P, nz, nx])."""
+                 stream=None, sources=None):
+        """Returns (misfit [P] float64, dJ/dv [P, nz, nx]). With sources (a
+        sequence of distinct source indices) both are sums over that minibatch
+        of sources only (fwi_gradient_sources)."""
         torch = _torch()
         v, P = self._models(v)
         if misfit is None:
@@ -159,11 +161,22 @@ class Fwi:
             grad = torch.empty((P, self.nz, self.nx), device=v.device, dtype=torch.float32)
         if tuple(dobs.shape) != (self.S, self.R, self.nt):
             raise ValueError("dobs must be [S, R, nt]")
-        check(self._L.fwi_gradient(self._h, _ptr(v, torch.float32, "v"), P,
-                                   _ptr(dobs, torch.float32, "dobs"), float(sigma),
-                                   _ptr(misfit, torch.float64, "misfit"),
-                                   _ptr(grad, torch.float32, "grad"), int(precision),
-                                   _stream(stream)), "fwi_gradient")
+        if sources is None:
+            check(self._L.fwi_gradient(self._h, _ptr(v, torch.float32, "v"), P,
+                                       _ptr(dobs, torch.float32, "dobs"), float(sigma),
+                                       _ptr(misfit, torch.float64, "misfit"),
+                                       _ptr(grad, torch.float32, "grad"), int(precision),
+                                       _stream(stream)), "fwi_gradient")
+        else:
+            src = [int(s) for s in sources]
+            arr = (ctypes.c_int * len(src))(*src)
+            check(self._L.fwi_gradient_sources(self._h, _ptr(v, torch.float32, "v"), P,
+                                               _ptr(dobs, torch.float32, "dobs"), float(sigma),
+                                               ctypes.cast(arr, ctypes.c_void_p), len(src),
+                                               _ptr(misfit, torch.float64, "misfit"),
+                                               _ptr(grad, torch.float32, "grad"),
+                                               int(precision), _stream(stream)),
+                  "fwi_gradient_sources")
         return misfit, grad
 
     def adjoint(self, v, dseis, precision=FWI_FP32, grad=None, stream=None):

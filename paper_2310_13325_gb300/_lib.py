@@ -37,6 +37,8 @@ _SIGS = {
     "fwi_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "fwi_gradient": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_double, c_void_p,
                              c_void_p, c_int, c_void_p]),
+    "fwi_gradient_sources": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_double, c_void_p,
+                                     c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "fwi_adjoint": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int,
                             c_void_p]),
     "fwi_last_status": (c_int, [c_void_p]),

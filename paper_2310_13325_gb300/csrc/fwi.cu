@@ -56,7 +56,7 @@ struct Tables {
 };
 
 struct GraphEntry {
-  std::array<uintptr_t, 12> key;
+  std::array<uintptr_t, 13> key;
   cudaGraphExec_t exec;
 };
 
@@ -80,13 +80,17 @@ struct fwi_ctx {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
-  std::map<std::tuple<int, int, int>, std::array<int, 4>> tuned;   // (P,mode,dtype) -> Q,V,T,gw
+  std::map<std::tuple<int, int, int>, std::array<int, 4>> tuned;   // (P, mode*16+dtype, S) -> Q,V,T,gw
   int force_Q = 0, force_V = 0, force_T = 0, force_spi = 0;          // launch override
   int force_coeff = 0;   // 0 any, 1 coefficients in shared memory, 2 in global memory
   int use_graphs = 1;   // VIPGB_GRAPHS=0 in the environment: eager launches
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
   int *pl_recmap = nullptr;
+  // source minibatches (fwi_gradient_sources): the chosen sources' positions
+  // and observed traces, gathered in front of a call, sized for all sources
+  int *d_sub_z = nullptr, *d_sub_x = nullptr;
+  float *d_sub_dobs = nullptr;
   double *pl_J = nullptr;
 };
 
@@ -345,7 +349,7 @@ static int choose_plan(fwi_ctx *c, int P, int mode, int dtype, Plan &out) {
   std::vector<Plan> cand;
   int rc = make_candidates(c, P, mode, dtype, cand);
   if (rc) return rc;
-  auto key = std::make_tuple(P, mode, dtype);
+  auto key = std::make_tuple(P, mode * 16 + dtype, c->S);
   auto it = c->tuned.find(key);
   const Plan *pick = nullptr;
   if (c->force_Q || c->force_spi) {
@@ -510,7 +514,7 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
 static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float *dobs,
                        const float *dseis, double sigma, double *misfit, float *grad,
                        float *seis, int dtype, cudaStream_t st) {
-  if (c->autotune && !c->tuned.count(std::make_tuple(P, mode, dtype))) {
+  if (c->autotune && !c->tuned.count(std::make_tuple(P, mode * 16 + dtype, c->S))) {
     int rc = autotune_plan(c, P, mode, dtype, v, dobs, dseis, sigma, st);
     if (rc) return rc;
   }
@@ -530,8 +534,9 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
   // graph replay keyed by everything the launch depends on
   uint64_t sigma_bits;
   memcpy(&sigma_bits, &sigma, 8);
-  std::array<uintptr_t, 12> key = {
-      (uintptr_t)mode, (uintptr_t)P, (uintptr_t)dtype, (uintptr_t)v, (uintptr_t)dobs,
+  std::array<uintptr_t, 13> key = {
+      (uintptr_t)mode | ((uintptr_t)c->S << 8), (uintptr_t)c->d_src_z,
+      (uintptr_t)P, (uintptr_t)dtype, (uintptr_t)v, (uintptr_t)dobs,
       (uintptr_t)dseis, (uintptr_t)seis, (uintptr_t)misfit, (uintptr_t)grad,
       (uintptr_t)sigma_bits,
       ((uintptr_t)pl.Q << 32) | ((uintptr_t)pl.V << 16) | (uintptr_t)pl.T,
@@ -630,7 +635,7 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
   cudaFree(tmp_out);
   cudaFree(tmp_mis);
   if (rc) return rc;
-  c->tuned[std::make_tuple(P, mode, dtype)] = pick;
+  c->tuned[std::make_tuple(P, mode * 16 + dtype, c->S)] = pick;
   (void)sigma;
   return VIP_OK;
 }
@@ -912,6 +917,7 @@ void fwi_destroy(fwi_ctx *c) {
   cudaFree(c->d_wavelet); cudaFree(c->d_src_z); cudaFree(c->d_src_x); cudaFree(c->d_status);
   cudaFree(c->pl_W); cudaFree(c->pl_a); cudaFree(c->pl_Gm); cudaFree(c->pl_gz);
   cudaFree(c->pl_gx); cudaFree(c->pl_recmap); cudaFree(c->pl_J);
+  cudaFree(c->d_sub_z); cudaFree(c->d_sub_x); cudaFree(c->d_sub_dobs);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
@@ -980,6 +986,43 @@ int fwi_gradient(fwi_ctx *c, const float *v, int P, const float *dobs, double si
   }
   return run_batched(c, WM_GRADIENT, v, P, dobs, nullptr, sigma, misfit, grad, nullptr,
                      precision, stream);
+}
+
+int fwi_gradient_sources(fwi_ctx *c, const float *v, int P, const float *dobs, double sigma,
+                         const int *sources, int nb, double *misfit, float *grad,
+                         int precision, vip_stream_t stream) {
+  int rc = check_call(c, v, P);
+  if (rc) return rc;
+  if (!dobs || !grad || !sources || nb < 1 || nb > c->S || !(sigma > 0) ||
+      precision < FWI_FP32 || precision > FWI_CKPT_FP16)
+    return VIP_ERR_ARG;
+  for (int k = 0; k < nb; ++k)
+    if (sources[k] < 0 || sources[k] >= c->S) return VIP_ERR_ARG;
+  if (c->mode == FWI_MODE_PLAIN) return VIP_ERR_UNSUPPORTED;
+  const size_t trace = (size_t)c->R * c->N;
+  if (!c->d_sub_z) {
+    VIP_TRY(cudaMalloc(&c->d_sub_z, sizeof(int) * c->S));
+    VIP_TRY(cudaMalloc(&c->d_sub_x, sizeof(int) * c->S));
+    VIP_TRY(cudaMalloc(&c->d_sub_dobs, sizeof(float) * trace * c->S));
+  }
+  // gather the minibatch in front of the launch, in stream order (a copy from
+  // pageable host memory returns once the source has been staged, so sz, sx
+  // may go out of scope)
+  std::vector<int> sz(nb), sx(nb);
+  for (int k = 0; k < nb; ++k) { sz[k] = c->src_z[sources[k]]; sx[k] = c->src_x[sources[k]]; }
+  VIP_TRY(cudaMemcpyAsync(c->d_sub_z, sz.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, stream));
+  VIP_TRY(cudaMemcpyAsync(c->d_sub_x, sx.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, stream));
+  for (int k = 0; k < nb; ++k)
+    VIP_TRY(cudaMemcpyAsync(c->d_sub_dobs + k * trace, dobs + (size_t)sources[k] * trace,
+                            sizeof(float) * trace, cudaMemcpyDeviceToDevice, stream));
+  // the batched path sees a problem with nb sources
+  const int S0 = c->S;
+  int *z0 = c->d_src_z, *x0 = c->d_src_x;
+  c->S = nb; c->d_src_z = c->d_sub_z; c->d_src_x = c->d_sub_x;
+  rc = run_batched(c, WM_GRADIENT, v, P, c->d_sub_dobs, nullptr, sigma, misfit, grad, nullptr,
+                   precision, stream);
+  c->S = S0; c->d_src_z = z0; c->d_src_x = x0;
+  return rc;
 }
 
 int fwi_adjoint(fwi_ctx *c, const float *v, int P, const float *dseis, float *grad,
