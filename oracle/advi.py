@@ -133,3 +133,53 @@ def advi_step_opt(mu, omega, state, t, eta, gm, lr, opt, a=None, b=None):
     mu, s1m, s2m = ascend(mu, gmu, s1m, s2m, t, lr, opt)
     omega, s1o, s2o = ascend(omega, gom, s1o, s2o, t, lr, opt)
     return mu, omega, (s1m, s2m, s1o, s2o)
+
+
+# ---------------------------------------------------------------------------
+# Full-rank ADVI restricted to a low-rank-plus-diagonal covariance (Eq. 7-11;
+# the full d x d factor L is out of reach at d = 36,000-144,000):
+#   theta = mu + e^omega * eta + B eps,   eta ~ N(0, I_d), eps ~ N(0, I_r),
+#   Sigma = diag(e^{2 omega}) + B B^T   (B [d, r]).
+# With g_s the per-sample gradient of log p(T^{-1}(theta)) + log|det J| as in
+# the mean-field case, the ELBO = E[...] + 1/2 log|Sigma| + const has
+#   grad_mu    = mean_s g_s
+#   grad_omega = mean_s g_s eta_s e^omega + diag(Sigma^{-1}) e^{2 omega}
+#   grad_B     = mean_s g_s eps_s^T + Sigma^{-1} B
+# (d/domega_i of 1/2 log|Sigma| = 1/2 tr(Sigma^{-1} dSigma/domega_i) and
+# d/dB of 1/2 log|Sigma| = Sigma^{-1} B). Here Sigma^{-1} is formed and
+# inverted densely: plain and slow, for small d only.
+
+def sample_lowrank(mu, omega, B, eta, eps, a=None, b=None):
+    """m_s = T^{-1}(mu + e^omega eta_s + B eps_s); eta [S, d], eps [S, r]."""
+    theta = mu[None, :] + np.exp(omega)[None, :] * eta + eps @ B.T
+    if a is None:
+        return theta
+    return T_inv(theta, a[None, :], b[None, :])
+
+
+def elbo_gradients_lowrank(mu, omega, B, eta, eps, gm, a=None, b=None):
+    """Monte-Carlo (grad_mu, grad_omega, grad_B)."""
+    theta = mu[None, :] + np.exp(omega)[None, :] * eta + eps @ B.T
+    if a is None:
+        g = np.asarray(gm, dtype=np.float64)
+    else:
+        s = 1.0 / (1.0 + np.exp(-theta))
+        g = gm * (b - a)[None, :] * s * (1.0 - s) + (1.0 - 2.0 * s)
+    S = g.shape[0]
+    Sigma = np.diag(np.exp(2.0 * omega)) + B @ B.T
+    Sinv = np.linalg.inv(Sigma)
+    grad_mu = g.mean(axis=0)
+    grad_omega = (g * eta * np.exp(omega)[None, :]).mean(axis=0) + np.diag(Sinv) * np.exp(2.0 * omega)
+    grad_B = g.T @ eps / S + Sinv @ B
+    return grad_mu, grad_omega, grad_B
+
+
+def advi_lowrank_step(mu, omega, B, state, t, eta, eps, gm, lr, a=None, b=None):
+    """One low-rank-plus-diagonal ADVI iteration with Adam on mu, omega, B.
+    state = (m_mu, v_mu, m_omega, v_omega, m_B, v_B)."""
+    gmu, gom, gB = elbo_gradients_lowrank(mu, omega, B, eta, eps, gm, a, b)
+    m_mu, v_mu, m_om, v_om, m_B, v_B = state
+    mu, m_mu, v_mu = adam_ascent(mu, gmu, m_mu, v_mu, t, lr)
+    omega, m_om, v_om = adam_ascent(omega, gom, m_om, v_om, t, lr)
+    B, m_B, v_B = adam_ascent(B, gB, m_B, v_B, t, lr)
+    return mu, omega, B, (m_mu, v_mu, m_om, v_om, m_B, v_B)
