@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--minibatch", type=int, default=0,
                     help="ssvgd workload: gradients from this many uniformly drawn "
                          "sources per step (0 = all), scaled by S / minibatch")
+    ap.add_argument("--advi-rank", type=int, default=0,
+                    help="ADVI workload: covariance diag + B B^T with B of this rank "
+                         "(0 = mean field)")
     ap.add_argument("--advi-rule", default="adam", choices=["sgd", "adagrad", "adadelta", "adam"],
                     help="ascent rule of the ADVI workload")
     ap.add_argument("--no-plain", action="store_true")
@@ -417,12 +420,26 @@ def run_other_workload(args, torch):
         st = torch.zeros((4, d), device=dev)
         it = [0]
 
+        rank = args.advi_rank
+        if rank:
+            Bl = torch.zeros((d, rank), device=dev)
+            st_lr = torch.zeros(4 * d + 2 * d * rank, device=dev)
+            work = torch.empty(2 * rank * rank, dtype=torch.float64, device=dev)
+
         def step(rec=None):
             it[0] += 1
             eta = vg.philox_normal(P, d, seed=5, it=it[0], device=dev)
-            m = vg.advi_sample(mu, om, eta, a_t, b_t)
+            if rank:
+                epsl = vg.philox_normal(P, rank, seed=6, it=it[0], device=dev)
+                m = vg.advi_lowrank_sample(mu, om, Bl, eta, epsl, a_t, b_t)
+            else:
+                m = vg.advi_sample(mu, om, eta, a_t, b_t)
             _, g = fwi.gradient(m, dobs, sigma, precision=prec)
             if rec: rec[1].record()
+            if rank:
+                vg.advi_lowrank_step(mu, om, Bl, st_lr, it[0], eta, epsl, g.reshape(P, -1), 0.01,
+                                     a_t, b_t, gscale=-1.0, work=work)
+                return
             rule = {"sgd": vg.ASCENT_SGD, "adagrad": vg.ASCENT_ADAGRAD,
                     "adadelta": vg.ASCENT_ADADELTA, "adam": vg.ASCENT_ADAM}[args.advi_rule]
             lr = 1.0 if rule == vg.ASCENT_ADADELTA else 0.01
@@ -458,7 +475,9 @@ def run_other_workload(args, torch):
             "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
             "update": ("ssvgd_step n=2000 d=144000, %s kernel" % args.svgd_kernel
                        if args.workload == "ssvgd"
-                       else "advi_step S=64 d=144000, %s" % args.advi_rule)}
+                       else ("advi_lowrank_step S=64 d=144000 rank %d" % args.advi_rank
+                             if args.advi_rank else
+                             "advi_step S=64 d=144000, %s" % args.advi_rule))}
     if args.workload == "ssvgd":
         line["iteration_s_for_2000_particles"] = (2000.0 / P) * t_fwi * 1e-3 + t_upd * 1e-3
     print(json.dumps(line))

@@ -340,6 +340,33 @@ int  advi_step_opt(float *mu, float *omega, float *state, int t,
                    const float *a, const float *b, float lr, int rule,
                    vip_stream_t stream);
 
+/* Full-rank ADVI (Eq. 7-11) with the covariance restricted to low rank plus
+ * diagonal, Sigma = diag(e^{2 omega}) + B B^T, because the full d x d factor
+ * L is out of reach at d = 36,000-144,000:
+ *   theta_s = mu + e^omega eta_s + B eps_s,  m_s = T^{-1}(theta_s)  (Eq. 12)
+ *   grad_mu    = mean_s g_s
+ *   grad_omega = mean_s g_s eta_s e^omega + diag(Sigma^{-1}) e^{2 omega}
+ *   grad_B     = mean_s g_s eps_s^T + Sigma^{-1} B
+ * with g_s as in advi_step and Sigma^{-1} applied through the r x r matrix
+ * M = I + B^T diag(e^{-2 omega}) B (Woodbury); Adam ascent on mu, omega, B.
+ *   B      [d][r] (row-major, r <= VIP_ADVI_MAX_RANK)
+ *   eta    [S][d], eps [S][r] standard normal draws
+ *   state  [4 d + 2 d r] zero before the first step: Adam moments of mu,
+ *          omega (as advi_step) then of B ([d][r] each)
+ *   work   [2 r r] FP64 scratch (M and its inverse), caller-owned
+ * advi_lowrank_sample writes m_out [S][d]. With B = 0 the step equals
+ * advi_step up to rounding. Errors: VIP_ERR_ARG (sizes, r, S r too large for
+ * shared memory). */
+#define VIP_ADVI_MAX_RANK 32
+int  advi_lowrank_sample(const float *mu, const float *omega, const float *B, int r,
+                         const float *eta, const float *eps, int S, int d,
+                         const float *a, const float *b, float *m_out,
+                         vip_stream_t stream);
+int  advi_lowrank_step(float *mu, float *omega, float *B, int r, float *state,
+                       double *work, int t, const float *eta, const float *eps,
+                       const float *gm, float gscale, int S, int d, const float *a,
+                       const float *b, float lr, vip_stream_t stream);
+
 /* SVGD / sSVGD in the unconstrained space (Sec. 3, second strategy for the
  * uniform prior): particles theta = T(m) with the transform of Eq. (12),
  * T(m) = log(m - a) - log(b - m), T^{-1}(theta) = a + (b - a) / (1 + e^-theta),

@@ -25,7 +25,7 @@ FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
 VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
 
 __all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "svgd_inverse_variance",
-           "advi_step_opt", "to_unconstrained", "to_model", "unconstrained_gradient",
+           "advi_step_opt", "advi_lowrank_sample", "advi_lowrank_step", "to_unconstrained", "to_model", "unconstrained_gradient",
            "ASCENT_SGD", "ASCENT_ADAGRAD", "ASCENT_ADADELTA", "ASCENT_ADAM", "advi_sample", "advi_step",
            "philox_normal", "svgd_workspace_size", "svgd_sqdist", "svgd_step_noalloc", "FWI_FP32", "FWI_CKPT_BF16",
            "FWI_CKPT_FP16", "FWI_MODE_BATCHED", "FWI_MODE_PLAIN", "VIP_GRAM_BF16",
@@ -378,6 +378,46 @@ def advi_step_opt(mu, omega, state, t, eta, gm, lr, rule, a=None, b=None, gscale
                                     _ptr(gm, torch.float32, "gm"), float(gscale), S, d,
                                     _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
                                     float(lr), int(rule), _stream(stream)), "advi_step_opt")
+
+
+def advi_lowrank_sample(mu, omega, B, eta, eps, a=None, b=None, out=None, stream=None):
+    """m_s = T^{-1}(mu + e^omega eta_s + B eps_s); B [d, r], eta [S, d], eps [S, r]."""
+    torch = _torch()
+    S, d = eta.shape
+    r = B.shape[1]
+    if out is None:
+        out = torch.empty((S, d), dtype=torch.float32, device=mu.device)
+    check(_lib.load().advi_lowrank_sample(_ptr(mu, torch.float32, "mu"),
+                                          _ptr(omega, torch.float32, "omega"),
+                                          _ptr(B, torch.float32, "B"), r,
+                                          _ptr(eta, torch.float32, "eta"),
+                                          _ptr(eps, torch.float32, "eps"), S, d,
+                                          _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                          _ptr(out, torch.float32, "m"), _stream(stream)),
+          "advi_lowrank_sample")
+    return out
+
+
+def advi_lowrank_step(mu, omega, B, state, t, eta, eps, gm, lr, a=None, b=None, gscale=1.0,
+                      work=None, stream=None):
+    """In-place Adam ascent of (mu, omega, B) for Sigma = diag(e^{2 omega}) + B B^T;
+    state [4 d + 2 d r] zero-initialised. Returns the FP64 work buffer (reusable)."""
+    torch = _torch()
+    S, d = eta.shape
+    r = B.shape[1]
+    if work is None:
+        work = torch.empty(2 * r * r, dtype=torch.float64, device=mu.device)
+    check(_lib.load().advi_lowrank_step(_ptr(mu, torch.float32, "mu"),
+                                        _ptr(omega, torch.float32, "omega"),
+                                        _ptr(B, torch.float32, "B"), r,
+                                        _ptr(state, torch.float32, "state"),
+                                        _ptr(work, torch.float64, "work"), int(t),
+                                        _ptr(eta, torch.float32, "eta"),
+                                        _ptr(eps, torch.float32, "eps"),
+                                        _ptr(gm, torch.float32, "gm"), float(gscale), S, d,
+                                        _ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"),
+                                        float(lr), _stream(stream)), "advi_lowrank_step")
+    return work
 
 
 def to_unconstrained(m, a, b, out=None, stream=None):

@@ -70,6 +70,11 @@ _SIGS = {
     "vip_to_model": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "vip_unconstrained_gradient": (c_int, [c_void_p, c_void_p, c_float, c_void_p, c_void_p,
                                            c_int, c_int, c_void_p, c_void_p]),
+    "advi_lowrank_sample": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                    c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "advi_lowrank_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int,
+                                  c_void_p, c_void_p, c_void_p, c_float, c_int, c_int, c_void_p,
+                                  c_void_p, c_float, c_void_p]),
     "vip_philox_normal": (c_int, [c_void_p, c_int, c_int, c_uint64, c_uint64, c_void_p]),
 }
 

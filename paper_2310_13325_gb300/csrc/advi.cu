@@ -144,6 +144,153 @@ __global__ void unconstrained_gradient_kernel(const float *theta, const float *g
   g[k] = fmaf(gscale * gm[k] * (b[c] - a[c]), sg * (1.f - sg), 1.f - 2.f * sg);
 }
 
+// ---------------------------------------------------------------------------
+// Low-rank-plus-diagonal ADVI: theta = mu + e^omega eta + B eps, Sigma =
+// D + B B^T with D = diag(e^{2 omega}), B [d][r] row-major, eps [S][r].
+// The entropy terms need Sigma^{-1} only through M = I + B^T D^{-1} B (r x r):
+//   Sigma^{-1} B = D^{-1} B M^{-1}                       (Woodbury)
+//   diag(Sigma^{-1})_i = (1 - B_i M^{-1} B_i^T / D_i) / D_i
+// so grad_omega_i = mean_s g eta e^omega + 1 - B_i M^{-1} B_i^T / D_i and
+// grad_B_i = mean_s g eps^T + B_i M^{-1} / D_i.
+
+__global__ void lowrank_sample_kernel(const float *mu, const float *om, const float *B, int r,
+                                      const float *eta, const float *eps, int S, int d,
+                                      const float *a, const float *b, float *m) {
+  extern __shared__ float es[];   // eps [S][r]
+  for (int q = threadIdx.x; q < S * r; q += blockDim.x) es[q] = eps[q];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d) return;
+  float Bi[VIP_ADVI_MAX_RANK];
+  for (int k = 0; k < r; ++k) Bi[k] = B[(size_t)i * r + k];
+  const float mi = mu[i], si = expf(om[i]);
+  const float ai = a ? a[i] : 0.f, wi = a ? b[i] - a[i] : 0.f;
+  for (int s = 0; s < S; ++s) {
+    float th = fmaf(si, eta[(size_t)s * d + i], mi);
+    for (int k = 0; k < r; ++k) th = fmaf(Bi[k], es[s * r + k], th);
+    m[(size_t)s * d + i] = a ? fmaf(wi, 1.f / (1.f + expf(-th)), ai) : th;
+  }
+}
+
+// M_kl = delta_kl + sum_i B_ik B_il e^{-2 omega_i}: one block per (k, l <= k)
+// pair, FP64, fixed reduction order.
+__global__ void lowrank_m_kernel(const float *om, const float *B, int r, int d, double *M) {
+  __shared__ double red[32];
+  int p = blockIdx.x, k = 0;
+  while (p > k) { p -= k + 1; ++k; }
+  const int l = p;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x)
+    acc += (double)B[(size_t)i * r + k] * (double)B[(size_t)i * r + l] * exp(-2.0 * (double)om[i]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (k == l) t += 1.0;
+    M[k * r + l] = t;
+    M[l * r + k] = t;
+  }
+}
+
+// Minv = M^{-1} for the symmetric positive definite r x r M (one thread:
+// Cholesky M = L L^T, then columns of L^{-T} L^{-1}).
+__global__ void lowrank_minv_kernel(const double *M, int r, double *Minv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double L[VIP_ADVI_MAX_RANK * VIP_ADVI_MAX_RANK];
+  for (int q = 0; q < r * r; ++q) L[q] = 0.0;
+  for (int j = 0; j < r; ++j) {
+    double s = M[j * r + j];
+    for (int k = 0; k < j; ++k) s -= L[j * r + k] * L[j * r + k];
+    const double ljj = sqrt(s > 0.0 ? s : 1e-300);
+    L[j * r + j] = ljj;
+    for (int i = j + 1; i < r; ++i) {
+      double t = M[i * r + j];
+      for (int k = 0; k < j; ++k) t -= L[i * r + k] * L[j * r + k];
+      L[i * r + j] = t / ljj;
+    }
+  }
+  double y[VIP_ADVI_MAX_RANK];
+  for (int c = 0; c < r; ++c) {
+    for (int i = 0; i < r; ++i) {           // L y = e_c
+      double t = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= L[i * r + k] * y[k];
+      y[i] = t / L[i * r + i];
+    }
+    for (int i = r - 1; i >= 0; --i) {      // L^T x = y
+      double t = y[i];
+      for (int k = i + 1; k < r; ++k) t -= L[k * r + i] * Minv[k * r + c];
+      Minv[i * r + c] = t / L[i * r + i];
+    }
+  }
+}
+
+__global__ void lowrank_step_kernel(float *mu, float *om, float *B, int r, float *st,
+                                    const double *Minv, int t, const float *eta,
+                                    const float *eps, const float *gm, float gscale, int S,
+                                    int d, const float *a, const float *b, float lr) {
+  extern __shared__ float smem_lr[];
+  float *es = smem_lr;                                       // eps [S][r]
+  double *Mi = reinterpret_cast<double *>(smem_lr + ((S * r + 1) & ~1));   // [r][r]
+  for (int q = threadIdx.x; q < S * r; q += blockDim.x) es[q] = eps[q];
+  for (int q = threadIdx.x; q < r * r; q += blockDim.x) Mi[q] = Minv[q];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d) return;
+  float Bi[VIP_ADVI_MAX_RANK];
+  double gB[VIP_ADVI_MAX_RANK];
+  for (int k = 0; k < r; ++k) { Bi[k] = B[(size_t)i * r + k]; gB[k] = 0.0; }
+  const float mi = mu[i], si = expf(om[i]);
+  const float wi = a ? b[i] - a[i] : 0.f;
+  double gmu = 0.0, gom = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const float e = eta[(size_t)s * d + i];
+    float th = fmaf(si, e, mi);
+    for (int k = 0; k < r; ++k) th = fmaf(Bi[k], es[s * r + k], th);
+    float g = gscale * gm[(size_t)s * d + i];
+    if (a) {
+      const float sg = 1.f / (1.f + expf(-th));
+      g = fmaf(g * wi, sg * (1.f - sg), 1.f - 2.f * sg);
+    }
+    gmu += (double)g;
+    gom += (double)g * (double)e;
+    for (int k = 0; k < r; ++k) gB[k] += (double)g * (double)es[s * r + k];
+  }
+  // entropy terms through M^{-1}
+  const double Di = exp(2.0 * (double)om[i]);
+  double q = 0.0;
+  double BM[VIP_ADVI_MAX_RANK];
+  for (int k = 0; k < r; ++k) {
+    double t2 = 0.0;
+    for (int l = 0; l < r; ++l) t2 += (double)Bi[l] * Mi[l * r + k];
+    BM[k] = t2;
+    q += t2 * (double)Bi[k];
+  }
+  const float g_mu = (float)(gmu / S);
+  const float g_om = (float)(gom / S * (double)si + 1.0 - q / Di);
+  const float b1 = 0.9f, b2 = 0.999f, ae = 1e-8f;
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  float *m_mu = st, *v_mu = st + d, *m_om = st + 2 * (size_t)d, *v_om = st + 3 * (size_t)d;
+  float *m_B = st + 4 * (size_t)d, *v_B = m_B + (size_t)d * r;
+  float m1 = fmaf(b1, m_mu[i], (1.f - b1) * g_mu);
+  float m2 = fmaf(b2, v_mu[i], (1.f - b2) * g_mu * g_mu);
+  m_mu[i] = m1; v_mu[i] = m2;
+  mu[i] = mi + lr * (m1 / c1) / (sqrtf(m2 / c2) + ae);
+  m1 = fmaf(b1, m_om[i], (1.f - b1) * g_om);
+  m2 = fmaf(b2, v_om[i], (1.f - b2) * g_om * g_om);
+  m_om[i] = m1; v_om[i] = m2;
+  om[i] = om[i] + lr * (m1 / c1) / (sqrtf(m2 / c2) + ae);
+  for (int k = 0; k < r; ++k) {
+    const size_t o = (size_t)i * r + k;
+    const float g_b = (float)(gB[k] / S + BM[k] / Di);
+    m1 = fmaf(b1, m_B[o], (1.f - b1) * g_b);
+    m2 = fmaf(b2, v_B[o], (1.f - b2) * g_b * g_b);
+    m_B[o] = m1; v_B[o] = m2;
+    B[o] = Bi[k] + lr * (m1 / c1) / (sqrtf(m2 / c2) + ae);
+  }
+}
+
 }  // namespace vip
 
 using namespace vip;
@@ -222,6 +369,37 @@ int vip_unconstrained_gradient(const float *theta, const float *gm, float gscale
   const size_t nd = (size_t)n * d;
   unconstrained_gradient_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, stream>>>(
       theta, gm, gscale, a, b, nd, d, g);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+int advi_lowrank_sample(const float *mu, const float *omega, const float *B, int r,
+                        const float *eta, const float *eps, int S, int d, const float *a,
+                        const float *b, float *m_out, vip_stream_t stream) {
+  if (!mu || !omega || !B || !eta || !eps || !m_out || S < 1 || d < 1 || r < 1 ||
+      r > VIP_ADVI_MAX_RANK || (!a) != (!b) || (size_t)S * r * 4 > 48 * 1024)
+    return VIP_ERR_ARG;
+  lowrank_sample_kernel<<<idiv_up(d, 128), 128, (size_t)S * r * 4, stream>>>(
+      mu, omega, B, r, eta, eps, S, d, a, b, m_out);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+int advi_lowrank_step(float *mu, float *omega, float *B, int r, float *state, double *work,
+                      int t, const float *eta, const float *eps, const float *gm,
+                      float gscale, int S, int d, const float *a, const float *b, float lr,
+                      vip_stream_t stream) {
+  const size_t smem = (size_t)((S * r + 1) & ~1) * 4 + (size_t)r * r * 8;
+  if (!mu || !omega || !B || !state || !work || !eta || !eps || !gm || S < 1 || d < 1 ||
+      r < 1 || r > VIP_ADVI_MAX_RANK || t < 1 || (!a) != (!b) || smem > 48 * 1024)
+    return VIP_ERR_ARG;
+  double *M = work, *Minv = work + (size_t)r * r;
+  lowrank_m_kernel<<<r * (r + 1) / 2, 256, 0, stream>>>(omega, B, r, d, M);
+  VIP_CHECK_LAUNCH();
+  lowrank_minv_kernel<<<1, 32, 0, stream>>>(M, r, Minv);
+  VIP_CHECK_LAUNCH();
+  lowrank_step_kernel<<<idiv_up(d, 128), 128, smem, stream>>>(
+      mu, omega, B, r, state, Minv, t, eta, eps, gm, gscale, S, d, a, b, lr);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }

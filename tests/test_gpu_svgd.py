@@ -353,3 +353,47 @@ def test_svgd_in_unconstrained_space_matches_oracle(stochastic):
         vg.ssvgd_step(tht, g, eps, seed=0, it=0, xi=_t(xi))
         ref, _, _ = osvgd.ssvgd_step_unconstrained(th, gm, eps, xi, a, b)
     assert rel(tht.double().cpu().numpy() - th, ref - th) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# low-rank-plus-diagonal ADVI
+
+@pytest.mark.parametrize("bounded", [True, False])
+def test_advi_lowrank_sample_and_step_match_oracle(bounded):
+    d, S, r = 2000, 16, 4
+    mu, om, eta, gm, a, b = _advi_case(d, S, 51, bounded)
+    rng = np.random.default_rng(52)
+    B = (rng.standard_normal((d, r)) * 0.05).astype(np.float32).astype(np.float64)
+    eps = rng.standard_normal((S, r)).astype(np.float32).astype(np.float64)
+    ta = None if a is None else _t(a)
+    tb = None if b is None else _t(b)
+    m = vg.advi_lowrank_sample(_t(mu), _t(om), _t(B), _t(eta), _t(eps), ta, tb)
+    assert rel(m.cpu().numpy(), oadvi.sample_lowrank(mu, om, B, eta, eps, a, b)) <= 1e-6
+    st = torch.zeros(4 * d + 2 * d * r, device=DEV)
+    mut, omt, Bt = _t(mu), _t(om), _t(B)
+    state = tuple(np.zeros_like(x) for x in (mu, mu, om, om, B, B))
+    mur, omr, Br = mu.copy(), om.copy(), B.copy()
+    work = None
+    for t in (1, 2, 3):
+        work = vg.advi_lowrank_step(mut, omt, Bt, st, t, _t(eta), _t(eps), _t(gm), 0.01, ta, tb,
+                                    work=work)
+        mur, omr, Br, state = oadvi.advi_lowrank_step(mur, omr, Br, state, t, eta, eps, gm, 0.01,
+                                                      a, b)
+    assert rel(mut.double().cpu().numpy() - mu, mur - mu) <= 1e-5
+    assert rel(omt.double().cpu().numpy() - om, omr - om) <= 1e-5
+    assert rel(Bt.double().cpu().numpy() - B, Br - B) <= 1e-5
+
+
+def test_advi_lowrank_with_zero_B_is_meanfield_step():
+    d, S, r = 3000, 16, 3
+    mu, om, eta, gm, a, b = _advi_case(d, S, 53, True)
+    eps = _t(np.random.default_rng(54).standard_normal((S, r)))
+    st1 = torch.zeros((4, d), device=DEV)
+    st2 = torch.zeros(4 * d + 2 * d * r, device=DEV)
+    m1, o1, m2, o2 = _t(mu), _t(om), _t(mu), _t(om)
+    Bz = torch.zeros((d, r), device=DEV)
+    for t in (1, 2):
+        vg.advi_step(m1, o1, st1, t, _t(eta), _t(gm), 0.02, _t(a), _t(b))
+        vg.advi_lowrank_step(m2, o2, Bz.clone(), st2, t, _t(eta), eps, _t(gm), 0.02, _t(a), _t(b))
+    assert rel(m2.double().cpu().numpy() - mu, m1.double().cpu().numpy() - mu) <= 1e-6
+    assert rel(o2.double().cpu().numpy() - om, o1.double().cpu().numpy() - om) <= 1e-6
