@@ -241,8 +241,8 @@ int  svgd_step(float *X, const float *G, float gscale, int n, int d, float eps,
  * in device memory, reserved on every GPU that loads the library until the
  * process exits. Problems whose svgd_workspace_size(n, d, gram_precision, 0)
  * exceeds that size are rejected with VIP_ERR_NOMEM before any device call
- * (with VIP_GRAM_BF16X3: n = 8 particles up to d = 76,928, n = 64 up to
- * d = 61,184, n = 600 up to d = 7,953).
+ * (with VIP_GRAM_BF16X3: n = 8 particles up to d = 53,376, n = 64 up to
+ * d = 45,248, n = 600 up to d = 5,119).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture. All calls share the array and it keeps the

@@ -17,4 +17,15 @@ namespace vip {
 int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_bfloat16 *Xl,
                    int n, int dp, int np, int splits, float *parts, int *err, cudaStream_t st);
 
+// SVGD / sSVGD update on the tensor cores: X[i][c] <- clip(X[i][c] +
+// sum_k A[i][k] B[c][k] + rcoef[i] Xc[i][c] / sqrt(q_c), lo, hi) for i < n,
+// c < d, with A [np][Kp] and B [dp][Kp] each given as three BF16 pieces
+// (h, m, l) multiplied with the six-product split (FP32-class accuracy).
+// np, dp multiples of 128, Kp of 64; q, lo, hi may be NULL. err as for
+// gram_tc_launch.
+int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const B[3], int n,
+                     int d, int np, int dp, int Kp, const float *Xc, const float *rcoef,
+                     const float *q, const float *lo, const float *hi, float *X, int *err,
+                     cudaStream_t st);
+
 }  // namespace vip

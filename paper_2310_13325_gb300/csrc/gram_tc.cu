@@ -257,6 +257,129 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
   }
 }
 
+// ---------------------------------------------------------------------------
+// SVGD / sSVGD update on the tensor cores: one CTA computes a 128 x 128 tile
+// of D = A B^T with A [np][Kp] (rows: particles; columns: the kernel matrix
+// and, for sSVGD, the Cholesky factor) and B [dp][Kp] (rows: coordinates;
+// columns: the matching right-hand sides), both as three BF16 pieces and the
+// six-product split, the same pipeline as gram_tc_kernel over all 6 * KB
+// blocks, then applies the update in the epilogue:
+//   X[i][c] = clip(X[i][c] + D[i][c] + rcoef[i] Xc[i][c] / sqrt(q_c), lo, hi)
+// (q NULL: 1). Tiles are ordered with the particle tiles of one coordinate
+// tile adjacent, so its B rows are read once into L2.
+__global__ void __launch_bounds__(128, 1) update_tc_kernel(
+    const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap am,
+    const __grid_constant__ CUtensorMap al, const __grid_constant__ CUtensorMap bh,
+    const __grid_constant__ CUtensorMap bm, const __grid_constant__ CUtensorMap bl, int KB,
+    int MT, int n, int d, const float *__restrict__ Xc, const float *__restrict__ rcoef,
+    const float *__restrict__ q, const float *__restrict__ lo, const float *__restrict__ hi,
+    float *X, int *err) {
+  extern __shared__ __align__(1024) uint8_t usm_raw[];
+  uint8_t *ring = (uint8_t *)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ti = blockIdx.x % MT, tj = blockIdx.x / MT;
+  const int row = ti * 128 + warp * 32 + lane;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GT_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     su32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tmem_base;
+
+  const int n_iter = 6 * KB;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n_iter; ++i) {
+      const int s = i % GT_STAGES;
+      const uint32_t use = (uint32_t)(i / GT_STAGES);
+      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err)) { abort_flag = 1; break; }
+      if (*(volatile int *)&abort_flag) break;
+      const int pass = i / KB, kb = i - pass * KB;
+      const int pa = kPassA[pass], pb = kPassB[pass];
+      const CUtensorMap *ma = pa == 0 ? &ah : (pa == 1 ? &am : &al);
+      const CUtensorMap *mb = pb == 0 ? &bh : (pb == 1 ? &bm : &bl);
+      uint8_t *sa = ring + s * GT_STAGE_BYTES;
+      uint8_t *sb = sa + GT_TILE_BYTES;
+      mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
+      tma_load_2d(sa, ma, &full_bar[s], kb * 64, ti * 128);
+      tma_load_2d(sb, mb, &full_bar[s], kb * 64, tj * 128);
+    }
+  } else if (threadIdx.x == 32) {
+    for (int i = 0; i < n_iter; ++i) {
+      const int s = i % GT_STAGES;
+      const uint32_t use = (uint32_t)(i / GT_STAGES);
+      if (!mbar_wait(&full_bar[s], use & 1u, err)) { abort_flag = 1; break; }
+      tc_fence_after();
+      const uint32_t sa = su32(ring + s * GT_STAGE_BYTES);
+      const uint32_t sb = sa + GT_TILE_BYTES;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        umma(tacc, sdesc(sa + k * 32), sdesc(sb + k * 32), (i > 0 || k > 0) ? 1u : 0u);
+      umma_commit(&empty_bar[s]);
+    }
+    umma_commit(&done_bar);
+  }
+  __syncwarp();
+  const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err));
+  tc_fence_after();
+  if (done && !*(volatile int *)&abort_flag) {
+    const uint32_t lane_base = tacc + ((uint32_t)(warp * 32) << 16);
+    const float rc = row < n ? rcoef[row] : 0.f;
+    for (int ch = 0; ch < 4; ++ch) {
+      uint32_t r[32];
+      tmem_ld32(lane_base + ch * 32, r);   // all lanes take part
+      if (row < n) {
+        const int c0 = tj * 128 + ch * 32;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int c = c0 + jj;
+          if (c < d) {
+            const size_t g = (size_t)row * d + c;
+            const float xs = q ? Xc[g] * (float)(1.0 / sqrt((double)q[c])) : Xc[g];
+            // the move first (its two parts cancel in part), then one rounding
+            // at the particle's own magnitude
+            float x = X[g] + fmaf(rc, xs, __uint_as_float(r[jj]));
+            if (lo) x = fmaxf(x, lo[c]);
+            if (hi) x = fminf(x, hi[c]);
+            X[g] = x;
+          }
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0 && abort_flag) {
+    for (int s = 0; s < GT_STAGES && s < n_iter; ++s) {
+      const int last = ((n_iter - 1 - s) / GT_STAGES);
+      mbar_wait(&full_bar[s], (uint32_t)(last & 1), err);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tacc) : "memory");
+  }
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -306,6 +429,31 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   gram_tc_kernel<<<dim3(tiles, splits), 128, smem, st>>>(mh, mm, ml, KB, kper, total, np, parts,
                                                          err);
+  VIP_CHECK_LAUNCH();
+  return VIP_OK;
+}
+
+int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const Bm[3], int n,
+                     int d, int np, int dp, int Kp, const float *Xc, const float *rcoef,
+                     const float *q, const float *lo, const float *hi, float *X, int *err,
+                     cudaStream_t st) {
+  if (np % 128 || dp % 128 || Kp % 64 || n > np || d > dp) return VIP_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (((uintptr_t)A[k] & 15) || ((uintptr_t)Bm[k] & 15)) return VIP_ERR_ARG;
+  CUtensorMap ma[3], mb[3];
+  for (int k = 0; k < 3; ++k) {
+    int rc = make_map(&ma[k], A[k], Kp, np);
+    if (rc) return rc;
+    rc = make_map(&mb[k], Bm[k], Kp, dp);
+    if (rc) return rc;
+  }
+  const int MT = np / 128, NT = dp / 128;
+  const size_t smem = (size_t)GT_STAGES * GT_STAGE_BYTES + 1024;
+  VIP_TRY(cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  update_tc_kernel<<<MT * NT, 128, smem, st>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], Kp / 64,
+                                               MT, n, d, Xc, rcoef, q, lo, hi, X, err);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }

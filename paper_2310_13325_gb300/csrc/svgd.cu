@@ -48,7 +48,12 @@ struct SvgdWs {
   int *flag;
   float *K, *rs;
   float *Lk, *Xi;
+  // tensor-core update: A = [Kbar | Lk] and B = [Y | Z]^T as BF16 pieces
+  __nv_bfloat16 *Ua[3], *Ub[3];
+  float *rcoef;
   int np, dp, splits, M;
+  int unp, udp, uKp;
+  bool tcu;
 };
 
 static int gram_splits(int n, int d, int gp) {
@@ -61,7 +66,8 @@ static int gram_splits(int n, int d, int gp) {
   return std::max(1, std::min(s, kmax));
 }
 
-static size_t layout(int n, int d, int gp, int stochastic, void *base, size_t cap, SvgdWs &w) {
+static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base, size_t cap,
+                     SvgdWs &w) {
   Carve cv(base, cap);
   w.np = (n + 127) / 128 * 128;
   w.dp = (d + 63) / 64 * 64;
@@ -85,6 +91,15 @@ static size_t layout(int n, int d, int gp, int stochastic, void *base, size_t ca
   w.rs = cv.take<float>(n);
   w.Lk = cv.take<float>(stochastic ? (size_t)n * n : 0);
   w.Xi = cv.take<float>(stochastic ? (size_t)n * d : 0);
+  w.tcu = tcu;
+  w.unp = (n + 127) / 128 * 128;
+  w.udp = (d + 127) / 128 * 128;
+  w.uKp = ((stochastic ? 2 * n : n) + 63) / 64 * 64;
+  for (int k = 0; k < 3; ++k) {
+    w.Ua[k] = cv.take<__nv_bfloat16>(tcu ? (size_t)w.unp * w.uKp : 0);
+    w.Ub[k] = cv.take<__nv_bfloat16>(tcu ? (size_t)w.udp * w.uKp : 0);
+  }
+  w.rcoef = cv.take<float>(tcu ? n : 0);
   return cv.off;
 }
 
@@ -422,6 +437,83 @@ __global__ void philox_fill_kernel(float *out, int rows, int cols, uint64_t seed
 }
 
 // ---------------------------------------------------------------------------
+// Three-piece BF16 split x ~ h + m + l (each remainder exact in FP32).
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m,
+                                       __nv_bfloat16 &l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Operand A of the tensor-core update, [np][Kp]: row i = (Kbar_i, Lk_i) for
+// sSVGD or Kbar_i for SVGD, zero-padded.
+__global__ void split_a_kernel(const float *__restrict__ K, const float *__restrict__ Lk, int n,
+                               int np, int Kp, __nv_bfloat16 *Ah, __nv_bfloat16 *Am,
+                               __nv_bfloat16 *Al) {
+  const size_t tot = (size_t)np * Kp;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / Kp), k = (int)(q % Kp);
+    float v = 0.f;
+    if (i < n) {
+      if (k < n) v = K[(size_t)i * n + k];
+      else if (Lk && k < 2 * n) v = Lk[(size_t)i * n + (k - n)];
+    }
+    split3(v, Ah[q], Am[q], Al[q]);
+  }
+}
+
+// Operand B, [dp][Kp] (coordinates x particles, a transpose through shared
+// memory): column k < n holds Y_kc = (eps/n) (gscale G_kc / q_c -
+// Xc_kc / (sqrt(q_c) h^2)), columns n..2n-1 (sSVGD) Z = noise_scale Xi / sqrt(q_c).
+__global__ void split_b_kernel(const float *__restrict__ G, const float *__restrict__ Xc,
+                               const float *__restrict__ Xi, const double *h2p,
+                               const float *__restrict__ q, int n, int d, int dp, int Kp,
+                               float en, float gscale, float ns, __nv_bfloat16 *Bh,
+                               __nv_bfloat16 *Bm, __nv_bfloat16 *Bl) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const float inv_h2 = (float)(1.0 / h2p[0]);
+  for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
+    const int k = k0 + kk, c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (c < d) {
+      const double qc = q ? (double)q[c] : 1.0;
+      const float iq = q ? (float)(1.0 / qc) : 1.f, isq = q ? (float)(1.0 / sqrt(qc)) : 1.f;
+      if (k < n) {
+        const size_t g = (size_t)k * d + c;
+        v = en * (gscale * iq * G[g] - isq * inv_h2 * Xc[g]);
+      } else if (Xi && k < 2 * n) {
+        v = ns * isq * Xi[(size_t)(k - n) * d + c];
+      }
+    }
+    tile[kk][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
+    const int c = c0 + cc, k = k0 + threadIdx.x;
+    if (c < dp && k < Kp) {
+      const size_t o = (size_t)c * Kp + k;
+      split3(tile[threadIdx.x][cc], Bh[o], Bm[o], Bl[o]);
+    }
+  }
+}
+
+__global__ void rcoef_kernel(const float *rs, const double *h2p, int n, float en, float *rc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rc[i] = en * rs[i] * (float)(1.0 / h2p[0]);
+}
+
+// A bounded wait of the tensor-core update gave up: its tiles are unknown,
+// so every particle is marked NaN rather than left half-updated.
+__global__ void poison_kernel(const int *err, size_t nd, float *X) {
+  if (!(*err & 1)) return;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nd;
+       q += (size_t)gridDim.x * blockDim.x)
+    X[q] = __int_as_float(0x7fc00000);
+}
+
 // Fused update GEMM: per 64x64 tile of (particles x coordinates) accumulate
 // Kbar G, Kbar Xc and (sSVGD) Lk Xi over all particles j, then apply Eq. (17)
 // (and Eq. 22) with the bound reset.
@@ -558,19 +650,39 @@ static int check_args(const float *X, int n, int d, int gp, void *ws) {
   return VIP_OK;
 }
 
+// The update runs on the tensor cores (update_tc_launch) for the BF16 Gram
+// precisions, or as the SIMT FP32 update_kernel for VIP_GRAM_FP32 (the
+// reference path).
 static int run_svgd(float *X, const float *G, float gscale, const float *q, int n, int d,
                     float eps, float h2, const float *lo, const float *hi, int gp, void *ws,
                     size_t ws_bytes, double *h2_used, bool stochastic, uint64_t seed,
                     uint64_t it, const float *xi, double *tau_used, cudaStream_t st) {
   if (check_args(X, n, d, gp, ws) || !G || !(eps >= 0.f)) return VIP_ERR_ARG;
   SvgdWs w;
-  const size_t need = layout(n, d, gp, stochastic, ws, ws_bytes, w);
+  const size_t need = layout(n, d, gp, stochastic, gp != VIP_GRAM_FP32, ws, ws_bytes, w);
   if (need > ws_bytes) return VIP_ERR_NOMEM;
   int rc = distances(X, q, n, d, h2, gp, w, h2_used, st);
   if (rc) return rc;
   kbar_kernel<<<n, 256, 0, st>>>(w.D2, n, w.h2, w.K, w.rs);
   VIP_CHECK_LAUNCH();
   const dim3 ug(idiv_up(d, 64), idiv_up(n, 64));
+  const float en = eps / (float)n;
+  auto tc_update = [&](const float *Lk, const float *noise, float ns) -> int {
+    split_a_kernel<<<1024, 256, 0, st>>>(w.K, Lk, n, w.unp, w.uKp, w.Ua[0], w.Ua[1], w.Ua[2]);
+    VIP_CHECK_LAUNCH();
+    split_b_kernel<<<dim3(w.udp / 32, w.uKp / 32), dim3(32, 8), 0, st>>>(
+        G, w.Xc, noise, w.h2, q, n, d, w.udp, w.uKp, en, gscale, ns, w.Ub[0], w.Ub[1], w.Ub[2]);
+    VIP_CHECK_LAUNCH();
+    rcoef_kernel<<<idiv_up(n, 256), 256, 0, st>>>(w.rs, w.h2, n, en, w.rcoef);
+    VIP_CHECK_LAUNCH();
+    int rc2 = update_tc_launch(w.Ua, w.Ub, n, d, w.unp, w.udp, w.uKp, w.Xc, w.rcoef, q, lo, hi,
+                               X, w.flag + 2, st);
+    if (rc2) return rc2;
+    poison_kernel<<<1024, 256, 0, st>>>(w.flag + 2, (size_t)n * d, X);
+    VIP_CHECK_LAUNCH();
+    return VIP_OK;
+  };
+  if (!stochastic && w.tcu) return tc_update(nullptr, nullptr, 0.f);
   if (!stochastic) {
     update_kernel<false><<<ug, 256, 0, st>>>(w.K, G, w.Xc, nullptr, nullptr, w.rs, w.h2, n, d,
                                              eps, gscale, 0.f, q, lo, hi, X);
@@ -616,6 +728,12 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
     noise = w.Xi;
   }
   const float ns = (float)std::sqrt(2.0 * (double)eps / n);
+  if (w.tcu) {
+    rc = tc_update(w.Lk, noise, ns);
+    if (rc) return rc;
+    if (tau_used) VIP_TRY(cudaStreamSynchronize(st));
+    return VIP_OK;
+  }
   update_kernel<true><<<ug, 256, 0, st>>>(w.K, G, w.Xc, w.Lk, noise, w.rs, w.h2, n, d, eps, gscale,
                                           ns, q, lo, hi, X);
   VIP_CHECK_LAUNCH();
@@ -665,7 +783,8 @@ int svgd_step_noalloc(float *X, const float *G, float gscale, int n, int d, floa
     return VIP_ERR_ARG;
   SvgdWs w;
   // size check before any device call: oversize problems never touch the GPU
-  if (layout(n, d, gram_precision, 0, nullptr, 0, w) + 256 > kNoallocScratchBytes)
+  if (layout(n, d, gram_precision, 0, gram_precision != VIP_GRAM_FP32, nullptr, 0, w) + 256 >
+      kNoallocScratchBytes)
     return VIP_ERR_NOMEM;
   void *ws = nullptr;
   int rc = noalloc_scratch(&ws);
@@ -677,7 +796,8 @@ int svgd_step_noalloc(float *X, const float *G, float gscale, int n, int d, floa
 size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic) {
   if (n < 1 || d < 1) return 0;
   SvgdWs w;
-  return layout(n, d, gram_precision, stochastic, nullptr, 0, w) + 256;
+  return layout(n, d, gram_precision, stochastic, gram_precision != VIP_GRAM_FP32, nullptr, 0,
+                w) + 256;
 }
 
 int svgd_step(float *X, const float *G, float gscale, int n, int d, float eps, float h2,
@@ -723,7 +843,7 @@ int svgd_sqdist(const float *X, int n, int d, int gram_precision, double *D2,
                 double *h2_used, void *ws, size_t ws_bytes, vip_stream_t stream) {
   if (check_args(X, n, d, gram_precision, ws) || !D2) return VIP_ERR_ARG;
   SvgdWs w;
-  if (layout(n, d, gram_precision, 0, ws, ws_bytes, w) > ws_bytes) return VIP_ERR_NOMEM;
+  if (layout(n, d, gram_precision, 0, false, ws, ws_bytes, w) > ws_bytes) return VIP_ERR_NOMEM;
   int rc = distances(X, nullptr, n, d, 0.f, gram_precision, w, h2_used, stream);
   if (rc) return rc;
   const size_t nn = (size_t)n * n;
