@@ -81,6 +81,10 @@ typedef struct {
     const int *rec_ix;     /* host [R] physical column of each receiver      */
 } fwi_geom;
 
+/* An fwi_ctx is not thread-safe: calls on one context (its scratch memory,
+ * graphs, tuning cache and, during fwi_gradient_sources, its source tables)
+ * must come from one host thread at a time; separate contexts are
+ * independent. */
 typedef struct fwi_ctx fwi_ctx;
 
 /* Precision of the stored forward wavefield snapshots that the imaging
