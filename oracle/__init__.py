@@ -15,6 +15,9 @@ Inversion Package", arXiv 2310.13325):
           stochastic SVGD with Cholesky-correlated noise (Eq. 21-25)
   advi    logit transform (Eq. 12), mean-field ADVI gradients (Eq. 10-11)
           and Adam ascent (Sec. 2.2)
+  tomo    travel-time tomography (Sec. 4.1): first-order upwind eikonal
+          travel times by fast marching, misfit (Eq. 26) and its ray-traced
+          velocity gradient
   philox  the Philox-4x32-10 counter-based generator (Salmon et al. 2011)
           with Box-Muller, to reproduce the device noise stream
 
