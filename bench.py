@@ -65,12 +65,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--plan", default="",
+                    help="force the wave launch shape Q,V,T,coeff (cluster CTAs, rows per "
+                         "thread, threads, 1 = coefficients in shared / 2 = in global "
+                         "memory); profiling cases only")
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time steps (profiling cases only)")
-    ap.add_argument("--workload", default="svgd", choices=["svgd", "ssvgd", "advi"],
+    ap.add_argument("--workload", default="svgd", choices=["svgd", "ssvgd", "advi", "tomo"],
                     help="svgd: the batched SVGD step (default); ssvgd / advi: the "
                          "240x600, 40-source shape with the stochastic-SVGD or "
-                         "mean-field ADVI update")
+                         "mean-field ADVI update; tomo: the travel-time tomography "
+                         "SVGD iteration")
     return ap.parse_args()
 
 
@@ -173,6 +178,9 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     gram = vg.VIP_GRAM_BF16X3 if args.precision == "fp32" else vg.VIP_GRAM_BF16
     geo, fwi, X0, dobs_h, sigma, lo, hi = build_problem(cfg, P, rank, dev, vg, torch)
     fwi.set_autotune(not args.no_autotune)
+    if args.plan:
+        q, v, t, coeff = (int(x) for x in args.plan.split(","))
+        fwi.set_plan(q, v, t, 0, coeff=coeff)
     X = torch.tensor(X0, device=dev)
     dobs = torch.tensor(dobs_h, device=dev)
     lo_t = torch.tensor(lo.reshape(-1), dtype=torch.float32, device=dev)
@@ -483,6 +491,142 @@ def run_other_workload(args, torch):
     print(json.dumps(line))
 
 
+def tomo_cpu_baseline(cfg, sta, dobs, sig, X, seconds=10.0):
+    """The FP64 oracle as it stands on whole particles of the tomography
+    workload (every source, every ray) until about `seconds` have passed."""
+    from oracle import tomo as otomo
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        otomo.misfit_gradient(X[k % len(X)].reshape(cfg.ny, cfg.nx), cfg.h, sta, dobs, sig)
+        k += 1
+        t = time.perf_counter() - t0
+        if t >= seconds:
+            break
+    return {"value": k / t, "unit": "particle-gradients/s", "cores": 1, "kind": "oracle",
+            "sample": "%d whole particle gradients (%d sources, %d rays each) in %.1f s"
+                      % (k, cfg.n_stations - 1, cfg.n_pairs, t)}
+
+
+def run_tomo(args, torch):
+    """Travel-time tomography SVGD iteration (Sec. 4.1 shape: 40 x 37 nodes
+    of 0.33 degrees, 61 stations, 1830 station pairs, 500 particles, uniform
+    prior handled in the unconstrained space): the ray gradients of every
+    particle, the transform to theta, svgd_step and the transform back."""
+    import synth.tomo as st
+    import paper_2310_13325_gb300 as vg
+    from paper_2310_13325_gb300 import build as vbuild
+    vbuild.build()
+    cfg = st.tomo_config("tomo_uk")
+    P = args.particles or cfg.n_particles
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream()
+    sta = st.stations(cfg)
+    tm = vg.Tomo.from_config(cfg, sta)
+    sig_h = st.pair_sigma(cfg, sta).astype(np.float32)
+    sig = torch.tensor(sig_h, device=dev)
+    v_true = torch.tensor(st.true_group_velocity(cfg).astype(np.float32), device=dev)
+    clean = tm.traveltimes(v_true.reshape(1, -1))[0]
+    dobs = clean + sig * torch.tensor(st.unit_noise(tm.n_pairs).astype(np.float32), device=dev)
+    lo, hi = st.prior_bounds(cfg)
+    lo_t = torch.tensor(lo.reshape(-1), dtype=torch.float32, device=dev)
+    hi_t = torch.tensor(hi.reshape(-1), dtype=torch.float32, device=dev)
+    # the transform is undefined on the bounds: draws start just inside them
+    pad = 1e-4 * (cfg.vmax - cfg.vmin)
+    X0 = np.clip(st.particles_from_prior(cfg, P), cfg.vmin + pad,
+                 cfg.vmax - pad).astype(np.float32)
+    X = torch.tensor(X0, device=dev)
+    theta = vg.to_unconstrained(X, lo_t, hi_t)
+    gth = torch.empty_like(X)
+    misfit = torch.empty(P, dtype=torch.float64, device=dev)
+    grad = torch.empty((P, cfg.ny, cfg.nx), device=dev)
+    gram = vg.VIP_GRAM_BF16X3
+    ws = torch.empty(vg.svgd_workspace_size(P, cfg.d, gram, False), dtype=torch.uint8,
+                     device=dev)
+    h2 = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    box = {}
+
+    def update():
+        vg.unconstrained_gradient(theta, grad.reshape(P, -1), lo_t, hi_t, gscale=-1.0,
+                                  out=gth)
+        if "eps" not in box:
+            box["eps"] = 0.05 / max(gth.abs().max().item(), 1e-30)
+        vg.svgd_step(theta, gth, box["eps"], gram_precision=gram, ws=ws, h2_used=h2)
+        vg.to_model(theta, lo_t, hi_t, out=X)
+
+    def step():
+        tm.gradient(X, dobs, sig, misfit=misfit, grad=grad)
+        update()
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    assert tm.last_status() == 0
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    ev = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        tm.gradient(X, dobs, sig, misfit=misfit, grad=grad)
+        e[1].record(stream)
+        update()
+        e[2].record(stream)
+        ev.append(e)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    assert tm.last_status() == 0 and torch.isfinite(X).all().item()
+    t_step = float(np.mean([a.elapsed_time(c) for a, b, c in ev]))
+    t_grad = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
+    t_upd = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
+
+    # end to end with host buffers: particles and data in, particles and misfits out
+    Xh = torch.tensor(X0).pin_memory()
+    Dh = dobs.cpu().pin_memory()
+    Xo = torch.empty_like(Xh).pin_memory()
+    Jo = torch.empty(P, dtype=torch.float64).pin_memory()
+    e_ms = []
+    for k in range(max(2, args.steps // 2) + 1):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        X.copy_(Xh, non_blocking=True)
+        dobs.copy_(Dh, non_blocking=True)
+        vg.to_unconstrained(X, lo_t, hi_t, out=theta)
+        step()
+        Xo.copy_(X, non_blocking=True)
+        Jo.copy_(misfit, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e_ms.append(a.elapsed_time(b))
+    e2e = float(np.mean(e_ms))
+    line = {"metric": "tomography particle-gradients/s (SVGD iteration)",
+            "value": P / (t_step * 1e-3), "unit": "particle-gradients/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "SVGD travel-time tomography, 40x37 nodes of 0.33 deg, "
+                                   "%d stations, %d pairs, %d particles, unconstrained space"
+                                   % (cfg.n_stations, cfg.n_pairs, P),
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "gradient_ms_per_step": t_grad, "update_ms_per_step": t_upd,
+            "rays_per_s": P * cfg.n_pairs / (t_grad * 1e-3),
+            "eikonal_solves_per_s": P * (cfg.n_stations - 1) / (t_grad * 1e-3),
+            "gpu_launches": (2 + 1 + 24 + 1) * args.steps, "clocks": clocks,
+            "e2e": {"value": P / (e2e * 1e-3), "unit": "particle-gradients/s",
+                    "h2d_bytes_per_step": Xh.numel() * 4 + Dh.numel() * 4,
+                    "d2h_bytes_per_step": Xo.numel() * 4 + Jo.numel() * 8}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = tomo_cpu_baseline(cfg, sta, dobs.cpu().double().numpy(),
+                                                 sig_h.astype(np.float64), X0.astype(np.float64))
+    print(json.dumps(line))
+
+
 def reduce_over_ranks(t_ms, e2e_ms, device):
     """Slowest rank's step time and end-to-end time (max over ranks). Every
     rank runs an independent replica; no data crosses ranks."""
@@ -509,6 +653,9 @@ def main():
         run_reference(args, cfg, P, ws_, rank)
         return
     import torch
+    if args.workload == "tomo":
+        run_tomo(args, torch)
+        return
     if args.workload != "svgd":
         run_other_workload(args, torch)
         return

@@ -393,6 +393,61 @@ int  vip_unconstrained_gradient(const float *theta, const float *gm, float gscal
 int  vip_philox_normal(float *out, int rows, int cols, uint64_t seed,
                        uint64_t iter, vip_stream_t stream);
 
+/* ======================================================================
+ * Travel-time tomography (Sec. 4.1): group travel times between stations
+ * from the first-order upwind discretisation of the eikonal equation
+ * |grad T| = 1/v (the system fast marching solves, Rawlinson & Sambridge
+ * 2004), and the gradient of the Gaussian misfit (Eq. 26, one sigma per
+ * travel time) from rays traced through the travel-time field (Sec. 3).
+ *
+ * Units of this block: velocity km/s, spacing km, time s. Velocity lives on
+ * the nodes of a regular ny x nx grid, V[P][ny][nx] with x fastest; stations
+ * are node indices i * nx + j. Station s < ns - 1 is the source of the pairs
+ * (s, r), r > s; data arrays hold the ns (ns - 1) / 2 pairs s-major, pair
+ * (s, r) at s * ns - s (s + 1) / 2 + r - s - 1.
+ *
+ * Rays start at the receiver node and step half a node spacing against the
+ * bilinearly interpolated nodal travel-time gradient (central differences
+ * inside the grid, one-sided on its edge), clipped to the grid, until they
+ * are within half a spacing of the source (or after 8 (ny + nx) steps), then
+ * join it with a straight segment. Each segment adds its length times the
+ * bilinear weights of its midpoint to the ray's slowness kernel.
+ * ====================================================================== */
+typedef struct tomo_ctx tomo_ctx;
+
+/* stations: host array of n_stations distinct node indices (copied).
+ * Errors: VIP_ERR_ARG (ny, nx < 2, h <= 0, fewer than 2 stations, an index
+ * outside the grid or repeated), VIP_ERR_UNSUPPORTED (the grid does not fit
+ * one CTA's shared memory: (ny + 2)(nx + 2) + 4 ny nx floats), VIP_ERR_CUDA.
+ * Synchronous. The context is used by one host thread at a time. */
+int  tomo_create(int ny, int nx, double h, int n_stations, const int *stations,
+                 tomo_ctx **out);
+int  tomo_destroy(tomo_ctx *ctx);
+int  tomo_pair_count(const tomo_ctx *ctx);
+
+/* Predicted travel times T[P][npairs] for P velocity maps V[P][ny][nx].
+ * Errors: VIP_ERR_ARG (NULL with P > 0, P < 0), VIP_ERR_CUDA. */
+int  tomo_traveltimes(tomo_ctx *ctx, const float *V, int P, float *T,
+                      vip_stream_t stream);
+
+/* Misfit J[p] = sum_i (T_i - dobs_i)^2 / (2 sigma_i^2) (FP64, summed over
+ * sources in order) and grad[P][ny][nx] = dJ/dv from the rays, for P maps.
+ *   dobs, sigma [npairs]; T [P][npairs] optional output (NULL to skip).
+ * grad is overwritten (zeroed on the stream first, then accumulated with
+ * atomics, so its last bits may vary between runs). Scratch of P (ns - 1)
+ * doubles is owned by the context and grown on demand (the growth
+ * synchronises the stream). Errors: VIP_ERR_ARG, VIP_ERR_NOMEM,
+ * VIP_ERR_CUDA. */
+int  tomo_gradient(tomo_ctx *ctx, const float *V, int P, const float *dobs,
+                   const float *sigma, double *misfit, float *grad, float *T,
+                   vip_stream_t stream);
+
+/* Device status of the last call (synchronises its stream): VIP_OK,
+ * VIP_ERR_ARG if some velocity was not positive and finite, VIP_ERR_TIMEOUT
+ * if a travel-time field did not settle within ny * nx relaxation sweeps;
+ * the outputs of that call are then undefined. */
+int  tomo_last_status(tomo_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

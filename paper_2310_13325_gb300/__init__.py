@@ -12,6 +12,8 @@ Entry points follow the paper (Zhang & Curtis, arXiv 2310.13325):
                                              seismogram map
   svgd_step (Eq. 17), ssvgd_step (Eq. 22, 25), advi_sample / advi_step
   (Eq. 10-12, mean-field), philox_normal
+  Tomo.traveltimes / Tomo.gradient          travel-time tomography (Sec. 4.1):
+                                             eikonal travel times, ray gradient
 """
 import ctypes
 
@@ -24,7 +26,7 @@ FWI_FP32, FWI_CKPT_BF16, FWI_CKPT_FP16 = 0, 1, 2
 FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
 VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
 
-__all__ = ["Fwi", "FwiSeis", "svgd_step", "ssvgd_step", "svgd_inverse_variance",
+__all__ = ["Fwi", "FwiSeis", "Tomo", "svgd_step", "ssvgd_step", "svgd_inverse_variance",
            "advi_step_opt", "advi_lowrank_sample", "advi_lowrank_step", "to_unconstrained", "to_model", "unconstrained_gradient",
            "ASCENT_SGD", "ASCENT_ADAGRAD", "ASCENT_ADADELTA", "ASCENT_ADAM", "advi_sample", "advi_step",
            "philox_normal", "svgd_workspace_size", "svgd_sqdist", "svgd_step_noalloc", "FWI_FP32", "FWI_CKPT_BF16",
@@ -191,6 +193,82 @@ class Fwi:
                                   _ptr(grad, torch.float32, "grad"), int(precision),
                                   _stream(stream)), "fwi_adjoint")
         return grad
+
+
+class Tomo:
+    """Travel-time tomography context (wraps tomo_create): ny x nx nodes of
+    spacing h km, stations as node indices i * nx + j (Sec. 4.1)."""
+
+    def __init__(self, ny, nx, h, stations):
+        L = _lib.load()
+        self.ny, self.nx, self.h = int(ny), int(nx), float(h)
+        self._sta = np.ascontiguousarray(stations, dtype=np.int32)
+        self.ns = self._sta.size
+        h_ = ctypes.c_void_p()
+        check(L.tomo_create(self.ny, self.nx, self.h, self.ns,
+                            self._sta.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            ctypes.byref(h_)), "tomo_create")
+        self._h = h_
+        self._L = L
+        self.n_pairs = L.tomo_pair_count(h_)
+
+    @classmethod
+    def from_config(cls, cfg, stations):
+        return cls(cfg.ny, cfg.nx, cfg.h, stations)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.tomo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_status(self):
+        return self._L.tomo_last_status(self._h)
+
+    def _models(self, V):
+        d = self.ny * self.nx
+        if V.dim() == 1 and V.numel() == d or tuple(V.shape) == (self.ny, self.nx):
+            V = V.reshape(1, d)
+        elif not ((V.dim() == 2 and V.shape[1] == d) or
+                  (V.dim() == 3 and tuple(V.shape[1:]) == (self.ny, self.nx))):
+            raise ValueError("velocity maps must be [P, ny, nx] or [P, ny*nx]")
+        return V, int(V.shape[0])
+
+    def traveltimes(self, V, out=None, stream=None):
+        """Travel times [P, n_pairs] (s) of the station pairs, s-major."""
+        torch = _torch()
+        V, P = self._models(V)
+        if out is None:
+            out = torch.empty((P, self.n_pairs), device=V.device, dtype=torch.float32)
+        check(self._L.tomo_traveltimes(self._h, _ptr(V, torch.float32, "V"), P,
+                                       _ptr(out, torch.float32, "out"), _stream(stream)),
+              "tomo_traveltimes")
+        return out
+
+    def gradient(self, V, dobs, sigma, misfit=None, grad=None, T=None, stream=None):
+        """Misfit [P] (FP64) and dJ/dv [P, ny, nx] from rays (Eq. 26)."""
+        torch = _torch()
+        V, P = self._models(V)
+        if misfit is None:
+            misfit = torch.empty(P, device=V.device, dtype=torch.float64)
+        if grad is None:
+            grad = torch.empty((P, self.ny, self.nx), device=V.device, dtype=torch.float32)
+        for name, t in (("dobs", dobs), ("sigma", sigma)):
+            if t.numel() != self.n_pairs:
+                raise ValueError("%s must hold %d travel times" % (name, self.n_pairs))
+        check(self._L.tomo_gradient(self._h, _ptr(V, torch.float32, "V"), P,
+                                    _ptr(dobs, torch.float32, "dobs"),
+                                    _ptr(sigma, torch.float32, "sigma"),
+                                    _ptr(misfit, torch.float64, "misfit"),
+                                    _ptr(grad, torch.float32, "grad"),
+                                    _ptr(T, torch.float32, "T"), _stream(stream)),
+              "tomo_gradient")
+        return misfit, grad
 
 
 def _make_fwiseis():

@@ -76,6 +76,13 @@ _SIGS = {
                                   c_void_p, c_void_p, c_void_p, c_float, c_int, c_int, c_void_p,
                                   c_void_p, c_float, c_void_p]),
     "vip_philox_normal": (c_int, [c_void_p, c_int, c_int, c_uint64, c_uint64, c_void_p]),
+    "tomo_create": (c_int, [c_int, c_int, c_double, c_int, c_int_p, ctypes.POINTER(c_void_p)]),
+    "tomo_destroy": (c_int, [c_void_p]),
+    "tomo_pair_count": (c_int, [c_void_p]),
+    "tomo_traveltimes": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "tomo_gradient": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_void_p]),
+    "tomo_last_status": (c_int, [c_void_p]),
 }
 
 # Symbols every build exports (checked by the CPU test suite).
