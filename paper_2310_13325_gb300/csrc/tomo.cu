@@ -18,6 +18,7 @@
 namespace {
 
 constexpr int kTomoThreads = 256;
+constexpr int kSlots = 3;                 // register-held nodes per thread and colour
 constexpr float kRayStep = 0.5f;         // ray step, node spacings
 
 struct TomoArgs {
@@ -38,12 +39,15 @@ __device__ __forceinline__ int pair_index(int s, int r, int ns) {
 
 // Upwind time of one node from its smaller neighbour times a, b along the
 // two axes and f = h / v: the root t >= max of ((t-a)^+)^2 + ((t-b)^+)^2 = f^2.
+// The two-sided root takes its square root as q * rsqrt(q) (q >= f^2 > 0 there;
+// relative error a few 1e-7, far inside the travel-time tolerance).
 __device__ __forceinline__ float upwind(float a, float b, float f) {
   const float lo = fminf(a, b), hi = fmaxf(a, b);
   if (!(lo < CUDART_INF_F)) return CUDART_INF_F;
   const float dd = hi - lo;
   if (dd >= f) return lo + f;
-  return 0.5f * (lo + hi + sqrtf(2.f * f * f - dd * dd));
+  const float q = 2.f * f * f - dd * dd;
+  return 0.5f * (lo + hi + q * rsqrtf(q));
 }
 
 // Node k of colour c ((i + j) & 1 == c), k counted row-major within the colour.
@@ -86,7 +90,7 @@ __device__ __forceinline__ void add_segment(float *K, float py, float px, float 
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kTomoThreads)
+__global__ void __launch_bounds__(kTomoThreads, 6)
 tomo_kernel(TomoArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ny = a.ny, nx = a.nx, n = ny * nx, W = nx + 2, ns = a.ns;
@@ -117,20 +121,55 @@ tomo_kernel(TomoArgs a) {
   // every accepted change lowers a time, so the sweep ends at the fixed point)
   const int half = (n + 1) >> 1;                // colour-0 count bounds colour 1
   int it = 0;
-  for (; it < a.maxit; ++it) {
-    int changed = 0;
+  if (half <= kSlots * kTomoThreads) {
+    // grids up to 2 kSlots x 256 nodes: each thread keeps the padded offsets and
+    // h / v of its nodes in registers for the whole relaxation
+    int off[2][kSlots];
+    float fv[2][kSlots];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      for (int k = tid; k < half; k += kTomoThreads) {
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int m = 0; m < kSlots; ++m) {
+        const int k = tid + m * kTomoThreads;
         int i, j;
-        if (!colour_node(k, c, ny, nx, i, j)) continue;
-        float *t = Tp + (i + 1) * W + (j + 1);
-        const float tn = upwind(fminf(t[-1], t[1]), fminf(t[-W], t[W]), F[i * nx + j]);
-        if (tn < *t) { *t = tn; changed = 1; }
+        off[c][m] = -1;
+        fv[c][m] = 0.f;
+        if (k < half && colour_node(k, c, ny, nx, i, j)) {
+          off[c][m] = (i + 1) * W + (j + 1);
+          fv[c][m] = F[i * nx + j];
+        }
       }
-      __syncthreads();
+    for (; it < a.maxit; ++it) {
+      int changed = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int m = 0; m < kSlots; ++m) {
+          if (off[c][m] < 0) continue;
+          float *t = Tp + off[c][m];
+          const float tn = upwind(fminf(t[-1], t[1]), fminf(t[-W], t[W]), fv[c][m]);
+          if (tn < *t) { *t = tn; changed = 1; }
+        }
+        if (c == 0) __syncthreads();
+      }
+      if (!__syncthreads_or(changed)) break;
     }
-    if (!__syncthreads_or(changed)) break;
+  } else {
+    for (; it < a.maxit; ++it) {
+      int changed = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        for (int k = tid; k < half; k += kTomoThreads) {
+          int i, j;
+          if (!colour_node(k, c, ny, nx, i, j)) continue;
+          float *t = Tp + (i + 1) * W + (j + 1);
+          const float tn = upwind(fminf(t[-1], t[1]), fminf(t[-W], t[W]), F[i * nx + j]);
+          if (tn < *t) { *t = tn; changed = 1; }
+        }
+        if (c == 0) __syncthreads();
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
   }
   if (it == a.maxit && tid == 0) atomicOr(a.status, 1);
 
@@ -166,13 +205,14 @@ tomo_kernel(TomoArgs a) {
       float py = (float)ri, px = (float)rj;
       for (int st = 0; st < a.maxsteps; ++st) {
         const float dy = py - sy, dx = px - sx;
-        if (sqrtf(dy * dy + dx * dx) <= kRayStep) break;
+        if (dy * dy + dx * dx <= kRayStep * kRayStep) break;
         const Bilin b = bilin(py, px, ny, nx);
         const float gy = interp(GY, b, nx), gx = interp(GX, b, nx);
-        const float gn = sqrtf(gy * gy + gx * gx);
-        if (gn == 0.f) break;
-        const float qy = fminf(fmaxf(py - kRayStep * gy / gn, 0.f), (float)(ny - 1));
-        const float qx = fminf(fmaxf(px - kRayStep * gx / gn, 0.f), (float)(nx - 1));
+        const float g2 = gy * gy + gx * gx;
+        if (g2 == 0.f) break;
+        const float sc = kRayStep * rsqrtf(g2);       // step / |grad T|
+        const float qy = fminf(fmaxf(py - sc * gy, 0.f), (float)(ny - 1));
+        const float qx = fminf(fmaxf(px - sc * gx, 0.f), (float)(nx - 1));
         add_segment(K, py, px, qy, qx, w, ny, nx);
         py = qy;
         px = qx;

@@ -4,7 +4,9 @@ oracle, through the C ABI.
 Tolerances. The device relaxes the same upwind equations in FP32; each
 travel time is a chain of at most a few hundred node updates, each rounded
 once, so times agree to TOL_T = 4e-6 relative (an FP32 emulation of the
-relaxation stays within 2.1e-7). The misfit then differs by at most
+relaxation with exact square roots stays within 2.1e-7; the device's
+q * rsqrt(q) adds a few 1e-7 per update, relative to that update's
+increment only). The misfit then differs by at most
 sum_i |res_i| TOL_T T_i / sigma_i^2 plus FP32 rounding of the residuals.
 Ray gradients move continuously with the travel times (the traced field is
 interpolated from nodal gradients, so a perturbation shifts a ray without
@@ -105,6 +107,18 @@ def test_full_size_batch_on_sampled_particles():
     Jh, Gh, Th = J.cpu().numpy(), G.cpu().numpy(), T.cpu().numpy()
     _check_gradient(cfg, sta, sig, d, V, Jh[rows], Gh[rows], Th[rows], rows)
     assert np.all(np.isfinite(Jh)) and np.all(np.isfinite(Gh))
+
+
+def test_grid_beyond_the_register_slots():
+    # more than 2 x 3 x 256 nodes: the relaxation's general loop
+    cfg, sta, sig, d, V = _case(st.tomo_config("tomo_small").with_(ny=48, nx=50,
+                                                                   n_stations=5), 2, "smooth")
+    tm = vg.Tomo.from_config(cfg, sta)
+    T = torch.empty((len(V), tm.n_pairs), device=DEV)
+    J, G = tm.gradient(_t(V), _t(d), _t(sig), T=T)
+    assert tm.last_status() == 0
+    _check_gradient(cfg, sta, sig, d, V, J.cpu().numpy(), G.cpu().numpy(),
+                    T.cpu().numpy(), range(len(V)))
 
 
 def test_edge_stations_minimal_grid_and_empty_batch():
