@@ -71,6 +71,8 @@ def parse():
                          "memory); profiling cases only")
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time steps (profiling cases only)")
+    ap.add_argument("--tomo-method", default="svgd", choices=["svgd", "ssvgd", "advi"],
+                    help="update of the tomography workload")
     ap.add_argument("--workload", default="svgd", choices=["svgd", "ssvgd", "advi", "tomo"],
                     help="svgd: the batched SVGD step (default); ssvgd / advi: the "
                          "240x600, 40-source shape with the stochastic-SVGD or "
@@ -314,6 +316,18 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     return out
 
 
+# Kernels one svgd_step enqueues (three-piece BF16 Gram, tensor-core update):
+# centre, norms, gram_tc, d2_finish, median_init, 8 x median_hist, 8 x
+# median_select, bandwidth, kbar, split_a, split_b, rcoef, update_tc, poison.
+SVGD_STEP_LAUNCHES = 28
+
+
+def fwi_gradient_launches(plan, nsrc):
+    """The persistent wave kernel, the per-item gradient merge when several work
+    items share a particle, and the misfit reduction."""
+    return 1 + (nsrc // plan["sources_per_item"] > 1) + 1
+
+
 def measured_traffic(cell_updates):
     """DRAM bytes of one wave-kernel launch, scaled from the committed ncu
     capture by cell updates, or None when the kernel source has changed since
@@ -509,16 +523,20 @@ def tomo_cpu_baseline(cfg, sta, dobs, sig, X, seconds=10.0):
 
 
 def run_tomo(args, torch):
-    """Travel-time tomography SVGD iteration (Sec. 4.1 shape: 40 x 37 nodes
-    of 0.33 degrees, 61 stations, 1830 station pairs, 500 particles, uniform
-    prior handled in the unconstrained space): the ray gradients of every
-    particle, the transform to theta, svgd_step and the transform back."""
+    """Travel-time tomography iteration at the Sec. 4.1 shape (40 x 37 nodes of
+    0.33 degrees, 61 stations, 1830 station pairs, uniform prior handled in the
+    unconstrained space), with the paper's three methods:
+      svgd  - 500 particles: ray gradients, transform to theta, svgd_step, back;
+      ssvgd - 20 particles: the same with ssvgd_step (Philox noise);
+      advi  - 64 draws of the mean-field Gaussian in theta: advi_sample, ray
+              gradients, advi_step_opt (Adam)."""
     import synth.tomo as st
     import paper_2310_13325_gb300 as vg
     from paper_2310_13325_gb300 import build as vbuild
     vbuild.build()
+    method = args.tomo_method
     cfg = st.tomo_config("tomo_uk")
-    P = args.particles or cfg.n_particles
+    P = args.particles or {"svgd": cfg.n_particles, "ssvgd": 20, "advi": 64}[method]
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream()
     sta = st.stations(cfg)
@@ -541,22 +559,51 @@ def run_tomo(args, torch):
     misfit = torch.empty(P, dtype=torch.float64, device=dev)
     grad = torch.empty((P, cfg.ny, cfg.nx), device=dev)
     gram = vg.VIP_GRAM_BF16X3
-    ws = torch.empty(vg.svgd_workspace_size(P, cfg.d, gram, False), dtype=torch.uint8,
-                     device=dev)
+    ws = (torch.empty(vg.svgd_workspace_size(P, cfg.d, gram, method == "ssvgd"),
+                      dtype=torch.uint8, device=dev) if method != "advi" else None)
     h2 = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    box = {}
+    mu = torch.zeros(cfg.d, device=dev)              # standard Gaussian start in theta
+    om = torch.zeros(cfg.d, device=dev)
+    adam = torch.zeros((4, cfg.d), device=dev)
+    eta = torch.empty((P, cfg.d), device=dev)
+    box = {"it": 0}
+    S = cfg.n_stations - 1
+    nb = min(args.minibatch, S) if args.minibatch else S
+    draw = np.random.default_rng(11)
+
+    def gradient():
+        # a source minibatch sums nb of the S source stations' pairs; S / nb
+        # times it estimates the full-data gradient (Sec. 3 after Eq. 22)
+        srcs = np.sort(draw.choice(S, nb, replace=False)) if nb < S else None
+        tm.gradient(X, dobs, sig, misfit=misfit, grad=grad, sources=srcs)
+
+    def prepare():
+        if method == "advi":
+            box["it"] += 1
+            vg.philox_normal(P, cfg.d, seed=5, it=box["it"], out=eta, device=dev)
+            vg.advi_sample(mu, om, eta, lo_t, hi_t, out=X)
 
     def update():
-        vg.unconstrained_gradient(theta, grad.reshape(P, -1), lo_t, hi_t, gscale=-1.0,
+        if method == "advi":
+            vg.advi_step_opt(mu, om, adam, box["it"], eta, grad.reshape(P, -1), 0.01,
+                             vg.ASCENT_ADAM, lo_t, hi_t, gscale=-S / nb)
+            return
+        vg.unconstrained_gradient(theta, grad.reshape(P, -1), lo_t, hi_t, gscale=-S / nb,
                                   out=gth)
         if "eps" not in box:
             box["eps"] = 0.05 / max(gth.abs().max().item(), 1e-30)
-        vg.svgd_step(theta, gth, box["eps"], gram_precision=gram, ws=ws, h2_used=h2)
+        if method == "ssvgd":
+            box["it"] += 1
+            vg.ssvgd_step(theta, gth, box["eps"], seed=3, it=box["it"], gram_precision=gram,
+                          ws=ws, h2_used=h2)
+        else:
+            vg.svgd_step(theta, gth, box["eps"], gram_precision=gram, ws=ws, h2_used=h2)
         vg.to_model(theta, lo_t, hi_t, out=X)
 
     def step():
-        tm.gradient(X, dobs, sig, misfit=misfit, grad=grad)
+        prepare()
+        gradient()
         update()
 
     for _ in range(max(args.warmup, 3)):
@@ -572,7 +619,8 @@ def run_tomo(args, torch):
         flush.fill_(1)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
-        tm.gradient(X, dobs, sig, misfit=misfit, grad=grad)
+        prepare()
+        gradient()
         e[1].record(stream)
         update()
         e[2].record(stream)
@@ -584,43 +632,52 @@ def run_tomo(args, torch):
     t_grad = float(np.mean([a.elapsed_time(b) for a, b, c in ev]))
     t_upd = float(np.mean([b.elapsed_time(c) for a, b, c in ev]))
 
-    # end to end with host buffers: particles and data in, particles and misfits out
-    Xh = torch.tensor(X0).pin_memory()
-    Dh = dobs.cpu().pin_memory()
-    Xo = torch.empty_like(Xh).pin_memory()
+    # end to end with host buffers: the method's state and the data in, the
+    # state and the misfits out
+    state = [mu, om] if method == "advi" else [X]
+    hin = [t.cpu().pin_memory() for t in state] + [dobs.cpu().pin_memory()]
+    hout = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in state]
     Jo = torch.empty(P, dtype=torch.float64).pin_memory()
     e_ms = []
     for k in range(max(2, args.steps // 2) + 1):
         flush.fill_(1)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        X.copy_(Xh, non_blocking=True)
-        dobs.copy_(Dh, non_blocking=True)
-        vg.to_unconstrained(X, lo_t, hi_t, out=theta)
+        for dst, src in zip(state + [dobs], hin):
+            dst.copy_(src, non_blocking=True)
+        if method != "advi":
+            vg.to_unconstrained(X, lo_t, hi_t, out=theta)
         step()
-        Xo.copy_(X, non_blocking=True)
+        for dst, src in zip(hout, state):
+            dst.copy_(src, non_blocking=True)
         Jo.copy_(misfit, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize()
         if k > 0:
             e_ms.append(a.elapsed_time(b))
     e2e = float(np.mean(e_ms))
-    line = {"metric": "tomography particle-gradients/s (SVGD iteration)",
+    name = {"svgd": "SVGD", "ssvgd": "sSVGD", "advi": "ADVI (Adam)"}[method]
+    line = {"metric": "tomography particle-gradients/s (%s iteration)" % name,
             "value": P / (t_step * 1e-3), "unit": "particle-gradients/s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "SVGD travel-time tomography, 40x37 nodes of 0.33 deg, "
-                                   "%d stations, %d pairs, %d particles, unconstrained space"
-                                   % (cfg.n_stations, cfg.n_pairs, P),
+            "config": {"workload": "%s travel-time tomography, 40x37 nodes of 0.33 deg, "
+                                   "%d stations, %d pairs, %d %s, unconstrained space"
+                                   % (name, cfg.n_stations, cfg.n_pairs, P,
+                                      "samples" if method == "advi" else "particles"),
+                       "sources_per_gradient": nb,
                        "l2": "flushed between timed steps (256 MB write)"},
             "gradient_ms_per_step": t_grad, "update_ms_per_step": t_upd,
-            "rays_per_s": P * cfg.n_pairs / (t_grad * 1e-3),
-            "eikonal_solves_per_s": P * (cfg.n_stations - 1) / (t_grad * 1e-3),
-            "gpu_launches": (2 + 1 + 24 + 1) * args.steps, "clocks": clocks,
+            "eikonal_solves_per_s": P * nb / (t_grad * 1e-3),
+            "clocks": clocks,
             "e2e": {"value": P / (e2e * 1e-3), "unit": "particle-gradients/s",
-                    "h2d_bytes_per_step": Xh.numel() * 4 + Dh.numel() * 4,
-                    "d2h_bytes_per_step": Xo.numel() * 4 + Jo.numel() * 8}}
+                    "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in hin),
+                    "d2h_bytes_per_step": (sum(t.numel() * t.element_size() for t in hout)
+                                           + Jo.numel() * 8)}}
+    if method == "svgd":
+        # tomo_kernel, tomo_misfit_kernel, the transform pair and svgd_step
+        line["gpu_launches"] = (2 + 2 + SVGD_STEP_LAUNCHES) * args.steps
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = tomo_cpu_baseline(cfg, sta, dobs.cpu().double().numpy(),
                                                  sig_h.astype(np.float64), X0.astype(np.float64))
@@ -709,7 +766,8 @@ def main():
                      "note": "algorithmic 16 B per cell update; the fields stay in shared "
                              "memory, DRAM sees the stored snapshots only (traffic, "
                              "dram_gbs: ncu bytes per launch scaled by cell updates)"},
-        "gpu_launches": (2 + 24 + (args.svgd_kernel == "diag") +
+        "gpu_launches": (fwi_gradient_launches(res["plan"], cfg.nsrc) + SVGD_STEP_LAUNCHES +
+                         (args.svgd_kernel == "diag") +
                          2 * (args.svgd_space == "unconstrained")) * args.steps,
         "clocks": res["clocks"],
     }

@@ -436,11 +436,23 @@ int  tomo_traveltimes(tomo_ctx *ctx, const float *V, int P, float *T,
  * grad is overwritten (zeroed on the stream first, then accumulated with
  * atomics, so its last bits may vary between runs). Scratch of P (ns - 1)
  * doubles is owned by the context and grown on demand (the growth
- * synchronises the stream). Errors: VIP_ERR_ARG, VIP_ERR_NOMEM,
+ * synchronises the stream), so calls on different streams must not overlap. Errors: VIP_ERR_ARG, VIP_ERR_NOMEM,
  * VIP_ERR_CUDA. */
 int  tomo_gradient(tomo_ctx *ctx, const float *V, int P, const float *dobs,
                    const float *sigma, double *misfit, float *grad, float *T,
                    vip_stream_t stream);
+
+/* tomo_gradient over a minibatch of the source stations (the stochastic
+ * gradients of sSVGD from uniformly drawn data subsets, Sec. 3 after Eq. 22):
+ * misfit and gradient sum the pairs (s, r > s) of the nb distinct source
+ * stations listed in sources (host array, values in [0, ns - 2], copied in
+ * stream order), so ((ns - 1) / nb) times them estimates the full-data values
+ * without bias. The list is staged in context memory, so two such calls on
+ * different streams must not overlap. Errors: as tomo_gradient, VIP_ERR_ARG
+ * for a bad list. */
+int  tomo_gradient_sources(tomo_ctx *ctx, const float *V, int P, const float *dobs,
+                           const float *sigma, const int *sources, int nb,
+                           double *misfit, float *grad, vip_stream_t stream);
 
 /* Device status of the last call (synchronises its stream): VIP_OK,
  * VIP_ERR_ARG if some velocity was not positive and finite, VIP_ERR_TIMEOUT

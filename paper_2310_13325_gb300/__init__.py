@@ -250,8 +250,10 @@ class Tomo:
               "tomo_traveltimes")
         return out
 
-    def gradient(self, V, dobs, sigma, misfit=None, grad=None, T=None, stream=None):
-        """Misfit [P] (FP64) and dJ/dv [P, ny, nx] from rays (Eq. 26)."""
+    def gradient(self, V, dobs, sigma, misfit=None, grad=None, T=None, sources=None,
+                 stream=None):
+        """Misfit [P] (FP64) and dJ/dv [P, ny, nx] from rays (Eq. 26); sources
+        (host list of source stations) sums only their pairs (a minibatch)."""
         torch = _torch()
         V, P = self._models(V)
         if misfit is None:
@@ -261,6 +263,19 @@ class Tomo:
         for name, t in (("dobs", dobs), ("sigma", sigma)):
             if t.numel() != self.n_pairs:
                 raise ValueError("%s must hold %d travel times" % (name, self.n_pairs))
+        if sources is not None:
+            if T is not None:
+                raise ValueError("T is not reported for a source minibatch")
+            src = [int(k) for k in sources]
+            arr = (ctypes.c_int * len(src))(*src)
+            check(self._L.tomo_gradient_sources(self._h, _ptr(V, torch.float32, "V"), P,
+                                                _ptr(dobs, torch.float32, "dobs"),
+                                                _ptr(sigma, torch.float32, "sigma"),
+                                                ctypes.cast(arr, ctypes.c_void_p), len(src),
+                                                _ptr(misfit, torch.float64, "misfit"),
+                                                _ptr(grad, torch.float32, "grad"),
+                                                _stream(stream)), "tomo_gradient_sources")
+            return misfit, grad
         check(self._L.tomo_gradient(self._h, _ptr(V, torch.float32, "V"), P,
                                     _ptr(dobs, torch.float32, "dobs"),
                                     _ptr(sigma, torch.float32, "sigma"),

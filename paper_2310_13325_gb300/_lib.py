@@ -82,6 +82,8 @@ _SIGS = {
     "tomo_traveltimes": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "tomo_gradient": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p, c_void_p]),
+    "tomo_gradient_sources": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                      c_int, c_void_p, c_void_p, c_void_p]),
     "tomo_last_status": (c_int, [c_void_p]),
 }
 

@@ -26,7 +26,9 @@ struct TomoArgs {
   const int *sta;
   const float *dobs, *sigma;
   float *Tout;        // [P][npairs] or null
-  double *mpart;      // [P][ns-1] or null
+  double *mpart;      // [P][nsrc] or null
+  const int *slist;   // source stations of the launch (null: 0 .. ns-2)
+  int nsrc;           // sources per particle in the launch
   float *grad;        // [P][ny*nx] or null
   int ny, nx, ns, npairs, P, maxit, maxsteps;
   float h;
@@ -94,7 +96,8 @@ __global__ void __launch_bounds__(kTomoThreads, 6)
 tomo_kernel(TomoArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ny = a.ny, nx = a.nx, n = ny * nx, W = nx + 2, ns = a.ns;
-  const int s = blockIdx.x % (ns - 1), p = blockIdx.x / (ns - 1);
+  const int ks = blockIdx.x % a.nsrc, p = blockIdx.x / a.nsrc;
+  const int s = a.slist ? a.slist[ks] : ks;
   const int tid = threadIdx.x;
   double *red = (double *)smem_raw;                       // [32]
   float *Tp = (float *)(smem_raw + 32 * sizeof(double));  // [(ny+2)][(nx+2)]
@@ -228,7 +231,7 @@ tomo_kernel(TomoArgs a) {
     if (tid == 0) {
       double t = 0.0;
       for (int wi = 0; wi < kTomoThreads / 32; ++wi) t += red[wi];
-      a.mpart[(size_t)p * (ns - 1) + s] = t;
+      a.mpart[(size_t)p * a.nsrc + ks] = t;
     }
     // dJ/dv_k = -h K_k / v_k^2
     float *g = a.grad + (size_t)p * n;
@@ -262,6 +265,7 @@ struct tomo_ctx {
   int ny, nx, ns, npairs, maxit, maxsteps;
   float h;
   int *d_sta = nullptr;
+  int *d_slist = nullptr;     // minibatch source list
   int *d_status = nullptr;
   double *d_mpart = nullptr;
   size_t mpart_cap = 0;
@@ -298,11 +302,13 @@ int tomo_create(int ny, int nx, double h, int n_stations, const int *stations,
   c->maxit = ny * nx;                              // bounds the dependency depth
   c->maxsteps = (int)(4 * (ny + nx) / kRayStep);
   if (cudaMalloc(&c->d_sta, sizeof(int) * n_stations) != cudaSuccess ||
+      cudaMalloc(&c->d_slist, sizeof(int) * n_stations) != cudaSuccess ||
       cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemcpy(c->d_sta, stations, sizeof(int) * n_stations, cudaMemcpyHostToDevice) !=
           cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
     cudaFree(c->d_sta);
+    cudaFree(c->d_slist);
     cudaFree(c->d_status);
     delete c;
     return VIP_ERR_CUDA;
@@ -315,6 +321,7 @@ int tomo_destroy(tomo_ctx *c) {
   if (!c) return VIP_OK;
   cudaDeviceSynchronize();
   cudaFree(c->d_sta);
+  cudaFree(c->d_slist);
   cudaFree(c->d_status);
   cudaFree(c->d_mpart);
   delete c;
@@ -336,6 +343,8 @@ static TomoArgs tomo_args(tomo_ctx *c, const float *V, int P) {
   a.maxsteps = c->maxsteps;
   a.h = c->h;
   a.status = c->d_status;
+  a.slist = nullptr;
+  a.nsrc = c->ns - 1;
   return a;
 }
 
@@ -353,15 +362,10 @@ int tomo_traveltimes(tomo_ctx *c, const float *V, int P, float *T, vip_stream_t 
   return VIP_OK;
 }
 
-int tomo_gradient(tomo_ctx *c, const float *V, int P, const float *dobs, const float *sigma,
-                  double *misfit, float *grad, float *T, vip_stream_t stream) {
-  if (!c || P < 0 || (P > 0 && (!V || !dobs || !sigma || !misfit || !grad))) return VIP_ERR_ARG;
-  if ((long long)P * (c->ns - 1) > 0x7fffffffLL) return VIP_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  c->last_stream = st;
-  VIP_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
-  if (P == 0) return VIP_OK;
-  const size_t need = (size_t)P * (c->ns - 1);
+static int tomo_run_gradient(tomo_ctx *c, const float *V, int P, const float *dobs,
+                             const float *sigma, const int *slist, int nsrc, double *misfit,
+                             float *grad, float *T, cudaStream_t st) {
+  const size_t need = (size_t)P * nsrc;
   if (need > c->mpart_cap) {
     VIP_TRY(cudaStreamSynchronize(st));
     cudaFree(c->d_mpart);
@@ -377,11 +381,45 @@ int tomo_gradient(tomo_ctx *c, const float *V, int P, const float *dobs, const f
   a.Tout = T;
   a.mpart = c->d_mpart;
   a.grad = grad;
-  tomo_kernel<true><<<P * (c->ns - 1), kTomoThreads, tomo_smem(c->ny, c->nx, true), st>>>(a);
+  a.slist = slist;
+  a.nsrc = nsrc;
+  tomo_kernel<true><<<P * nsrc, kTomoThreads, tomo_smem(c->ny, c->nx, true), st>>>(a);
   VIP_CHECK_LAUNCH();
-  tomo_misfit_kernel<<<(P + 127) / 128, 128, 0, st>>>(c->d_mpart, P, c->ns - 1, misfit);
+  tomo_misfit_kernel<<<(P + 127) / 128, 128, 0, st>>>(c->d_mpart, P, nsrc, misfit);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
+}
+
+int tomo_gradient(tomo_ctx *c, const float *V, int P, const float *dobs, const float *sigma,
+                  double *misfit, float *grad, float *T, vip_stream_t stream) {
+  if (!c || P < 0 || (P > 0 && (!V || !dobs || !sigma || !misfit || !grad))) return VIP_ERR_ARG;
+  if ((long long)P * (c->ns - 1) > 0x7fffffffLL) return VIP_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  VIP_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+  if (P == 0) return VIP_OK;
+  return tomo_run_gradient(c, V, P, dobs, sigma, nullptr, c->ns - 1, misfit, grad, T, st);
+}
+
+int tomo_gradient_sources(tomo_ctx *c, const float *V, int P, const float *dobs,
+                          const float *sigma, const int *sources, int nb, double *misfit,
+                          float *grad, vip_stream_t stream) {
+  if (!c || P < 0 || (P > 0 && (!V || !dobs || !sigma || !misfit || !grad))) return VIP_ERR_ARG;
+  if (!sources || nb < 1 || nb > c->ns - 1) return VIP_ERR_ARG;
+  for (int k = 0; k < nb; ++k) {
+    if (sources[k] < 0 || sources[k] >= c->ns - 1) return VIP_ERR_ARG;
+    for (int m = 0; m < k; ++m)
+      if (sources[m] == sources[k]) return VIP_ERR_ARG;
+  }
+  if ((long long)P * nb > 0x7fffffffLL) return VIP_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  VIP_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+  if (P == 0) return VIP_OK;
+  // a copy from pageable host memory returns once the list has been staged,
+  // and the launch that reads it follows in stream order
+  VIP_TRY(cudaMemcpyAsync(c->d_slist, sources, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+  return tomo_run_gradient(c, V, P, dobs, sigma, c->d_slist, nb, misfit, grad, nullptr, st);
 }
 
 int tomo_last_status(tomo_ctx *c) {

@@ -121,6 +121,39 @@ def test_grid_beyond_the_register_slots():
                     T.cpu().numpy(), range(len(V)))
 
 
+def test_source_minibatch_matches_the_oracle_and_partitions():
+    cfg, sta, sig, d, V = _case(st.tomo_config("tomo_small"), 3, "smooth", seed=4)
+    tm = vg.Tomo.from_config(cfg, sta)
+    h = np.float32(cfg.h).astype(np.float64)
+    Vt, dt, st_ = _t(V), _t(d), _t(sig)
+    parts = ([0, 3, 6], [1, 2, 4, 5, 7])
+    Jf, Gf = tm.gradient(Vt, dt, st_)
+    Jf, Gf = Jf.cpu().numpy(), Gf.cpu().numpy().reshape(len(V), -1)
+    Js, Gs = 0.0, 0.0
+    ns = cfg.n_stations
+    To = [otomo.traveltimes(v.reshape(cfg.ny, cfg.nx), h, sta) for v in V]
+    for part in parts:
+        J, G = tm.gradient(Vt, dt, st_, sources=part)
+        assert tm.last_status() == 0
+        J, G = J.cpu().numpy(), G.cpu().numpy().reshape(len(V), -1)
+        mine = [otomo.pair_index(s, r, ns) for s in part for r in range(s + 1, ns)]
+        for p in range(len(V)):
+            Jo, go = otomo.misfit_gradient(V[p].reshape(cfg.ny, cfg.nx), h, sta, d, sig,
+                                           sources=part)
+            t = To[p][mine]
+            bound = np.sum(np.abs(t - d[mine]) * TOL_T * t / sig[mine] ** 2) + 1e-6 * Jo
+            assert abs(J[p] - Jo) <= bound
+            assert np.max(np.abs(G[p] - go.reshape(-1))) <= TOL_G * np.max(np.abs(go))
+        Js, Gs = Js + J, Gs + G
+    # the same per-source work, summed in another grouping: FP32 atomics only
+    np.testing.assert_allclose(Js, Jf, rtol=1e-12)
+    assert np.max(np.abs(Gs - Gf)) <= 1e-5 * np.max(np.abs(Gf))
+    with pytest.raises(vg.VipError):
+        tm.gradient(Vt, dt, st_, sources=[0, 0])
+    with pytest.raises(vg.VipError):
+        tm.gradient(Vt, dt, st_, sources=[cfg.n_stations - 1])
+
+
 def test_edge_stations_minimal_grid_and_empty_batch():
     # stations on corners and edges, adjacent stations, the smallest grid
     base = st.tomo_config("tomo_small")

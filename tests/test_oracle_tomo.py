@@ -174,3 +174,24 @@ def test_ray_gradient_follows_finite_differences():
     cos = np.sum(fd * g) / (np.linalg.norm(fd) * np.linalg.norm(g))
     assert cos > 0.85
     assert np.linalg.norm(g) / np.linalg.norm(fd) == pytest.approx(1.0, abs=0.35)
+
+
+def test_source_minibatches_partition_the_misfit_and_gradient():
+    # a partition of the source stations adds up to the full sums, and the
+    # (ns - 1) / nb scaled minibatch averaged over all subsets is the full value
+    import itertools
+    cfg = st.tomo_config("tomo_small").with_(ny=10, nx=12, n_stations=5)
+    sta = st.stations(cfg)
+    sig = st.pair_sigma(cfg, sta)
+    d = tomo.traveltimes(st.true_group_velocity(cfg), cfg.h, sta)
+    v = st.smooth_particles(cfg, 1, seed=9)[0].reshape(cfg.ny, cfg.nx)
+    J, g = tomo.misfit_gradient(v, cfg.h, sta, d, sig)
+    J1, g1 = tomo.misfit_gradient(v, cfg.h, sta, d, sig, sources=[0, 2])
+    J2, g2 = tomo.misfit_gradient(v, cfg.h, sta, d, sig, sources=[1, 3])
+    assert J1 + J2 == pytest.approx(J, rel=1e-13)
+    np.testing.assert_allclose(g1 + g2, g, rtol=1e-12, atol=1e-12 * np.abs(g).max())
+    S, nb = cfg.n_stations - 1, 2
+    subsets = list(itertools.combinations(range(S), nb))
+    Jm = np.mean([tomo.misfit_gradient(v, cfg.h, sta, d, sig, sources=list(c))[0]
+                  for c in subsets]) * S / nb
+    assert Jm == pytest.approx(J, rel=1e-12)
