@@ -393,16 +393,21 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
     else
       win[8] = c.bedge ? ld_cluster4(c.bot + (uint32_t)(i + 4 - V) * c.bstr) : ld4(rp + 4 * PX);
     const float4 Lf = ld4(rp - 4), Rf = ld4(rp + 4), C = win[4];
-    // cell pairs (0,1) and (2,3). The horizontal neighbour sums are formed
-    // lane by lane (scalar adds land directly in register pairs; pairing the
-    // odd-offset neighbours instead would need register moves)
+    // cell pairs (0,1) and (2,3). The horizontal neighbour sums at even
+    // offsets pair aligned register pairs and take one packed add; those at odd
+    // offsets are formed lane by lane (pairing them would need register moves)
     const float2 c01 = make_float2(C.x, C.y), c23 = make_float2(C.z, C.w);
     const float xs[12] = {Lf.x, Lf.y, Lf.z, Lf.w, C.x, C.y, C.z, C.w, Rf.x, Rf.y, Rf.z, Rf.w};
     float2 h01[4], h23[4], up01[4], dn01[4], up23[4], dn23[4];
 #pragma unroll
     for (int d = 1; d <= 4; ++d) {
-      h01[d - 1] = make_float2(__fadd_rn(xs[4 - d], xs[4 + d]), __fadd_rn(xs[5 - d], xs[5 + d]));
-      h23[d - 1] = make_float2(__fadd_rn(xs[6 - d], xs[6 + d]), __fadd_rn(xs[7 - d], xs[7 + d]));
+      if (d % 2 == 0) {
+        h01[d - 1] = add2(make_float2(xs[4 - d], xs[5 - d]), make_float2(xs[4 + d], xs[5 + d]));
+        h23[d - 1] = add2(make_float2(xs[6 - d], xs[7 - d]), make_float2(xs[6 + d], xs[7 + d]));
+      } else {
+        h01[d - 1] = make_float2(__fadd_rn(xs[4 - d], xs[4 + d]), __fadd_rn(xs[5 - d], xs[5 + d]));
+        h23[d - 1] = make_float2(__fadd_rn(xs[6 - d], xs[6 + d]), __fadd_rn(xs[7 - d], xs[7 + d]));
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
