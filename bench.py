@@ -296,24 +296,33 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
 
     # the plain per-step GPU loop on a sample (1 particle, 2 sources)
     if not args.no_plain and rank == 0:
-        sub = cfg.with_(nsrc=2)
-        geo2 = synth.geometry(cfg)
-        geo2 = dict(geo2, src_iz=geo2["src_iz"][:2], src_ix=geo2["src_ix"][[0, cfg.nsrc // 2]])
-        fp = vg.Fwi.from_config(sub, geo2)
-        fp.set_mode(vg.FWI_MODE_PLAIN, 1)
-        d2 = dobs[[0, cfg.nsrc // 2]].contiguous()
-        v1 = X[:1].clone()
-        fp.gradient(v1, d2, sigma)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fp.gradient(v1, d2, sigma)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t_pair = a.elapsed_time(b) / 2.0          # ms per (particle, source)
-        out["plain_particle_gradients_per_s"] = 1e3 / (t_pair * cfg.nsrc)
-        fp.close()
+        out["plain_particle_gradients_per_s"] = plain_rate(cfg, X[:1], dobs, sigma, vg, torch)
     return out
+
+
+def plain_rate(cfg, v1, dobs, sigma, vg, torch):
+    """Particle-gradients/s of the plain per-step FP32 loop (one launch per time
+    step, wavefields in global memory), timed on one particle and two of the
+    sources (the first and the middle one) and scaled to all sources."""
+    stream = torch.cuda.current_stream()
+    sub = cfg.with_(nsrc=2)
+    geo2 = synth.geometry(cfg)
+    geo2 = dict(geo2, src_iz=geo2["src_iz"][[0, cfg.nsrc // 2]],
+                src_ix=geo2["src_ix"][[0, cfg.nsrc // 2]])
+    fp = vg.Fwi.from_config(sub, geo2)
+    fp.set_mode(vg.FWI_MODE_PLAIN, 1)
+    d2 = dobs[[0, cfg.nsrc // 2]].contiguous()
+    v1 = v1.clone()
+    fp.gradient(v1, d2, sigma)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fp.gradient(v1, d2, sigma)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_pair = a.elapsed_time(b) / 2.0          # ms per (particle, source)
+    fp.close()
+    return 1e3 / (t_pair * cfg.nsrc)
 
 
 # Kernels one svgd_step enqueues (three-piece BF16 Gram, tensor-core update):
@@ -502,6 +511,11 @@ def run_other_workload(args, torch):
                              "advi_step S=64 d=144000, %s" % args.advi_rule))}
     if args.workload == "ssvgd":
         line["iteration_s_for_2000_particles"] = (2000.0 / P) * t_fwi * 1e-3 + t_upd * 1e-3
+    if not args.no_plain:
+        # the same gradients through the plain per-step FP32 loop
+        pr = plain_rate(cfg, torch.tensor(X0[:1], device=dev), dobs, sigma, vg, torch)
+        line["plain_particle_gradients_per_s"] = pr
+        line["batched_over_plain"] = line["value"] / pr
     print(json.dumps(line))
 
 
