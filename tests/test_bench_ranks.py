@@ -43,3 +43,14 @@ def test_two_gloo_ranks_reduce_to_the_slowest_rank():
         t, e, v = out[rank]
         assert t == 150.0 and e == 200.0
         assert v == pytest.approx(1200 / 0.150)
+
+
+def test_launch_count_of_a_gradient_plan():
+    # the wave kernel and the misfit reduction, plus the merge of per-item
+    # gradients when several work items share a particle
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    assert bench.fwi_gradient_launches({"sources_per_item": 2}, 20) == 3
+    assert bench.fwi_gradient_launches({"sources_per_item": 20}, 20) == 2
+    assert bench.SVGD_STEP_LAUNCHES == 28
