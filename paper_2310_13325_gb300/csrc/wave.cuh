@@ -339,7 +339,7 @@ __device__ __forceinline__ void add_lane(float2 &s01, float2 &s23, int j, float 
 // (floats) from c.cur: dn to the next level, dW to w', dG to the gradient
 // accumulator; PX is the row pitch of all four. With GW, w' and the
 // accumulator are instead read from global memory at wg, gg (row r0 of the
-// task, rows W4 apart), two rows ahead of their use. The vertical stencil
+// task, rows W4 apart), kAhead rows ahead of their use. The vertical stencil
 // window of 9 rows lives in registers; each row loads one new window row, its
 // left and right neighbour quadruples, w' and the previous value.
 template <int V, bool ADJ, bool SNAP, int MODE, class DT, bool GW>
@@ -350,20 +350,21 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
                                           const float *wg, float *gg, int W4, float2 k1,
                                           float2 k2, float2 k3, float2 k4, int tid) {
   using M = typename MaskT<V>::type;
+  constexpr int kAhead = 3;      // rows between a global load and its use
   float4 wq[V], gq[V];
   if (GW) {
 #pragma unroll
-    for (int i = 0; i < 2 && i < V; ++i) {
+    for (int i = 0; i < kAhead && i < V; ++i) {
       wq[i] = ld4(wg + i * W4);
       if (ADJ && SNAP) gq[i] = __ldcg(reinterpret_cast<const float4 *>(gg + i * W4));
     }
   }
-  // adjoint: snapshot rows are loaded two rows ahead of their use
+  // adjoint: snapshot rows are loaded kAhead rows ahead of their use
   float4 dq[V];
   float dinv[V];
   if (ADJ && SNAP) {
 #pragma unroll
-    for (int i = 0; i < 2 && i < V; ++i) {
+    for (int i = 0; i < kAhead && i < V; ++i) {
       dinv[i] = Snap<DT>::scaled ? Stask[i] : 1.f;
       dq[i] = Snap<DT>::ld(Dtask, (size_t)i * W4, 1.f);
     }
@@ -379,13 +380,13 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
   for (int j = 4; j < 8; ++j) win[j] = ld4(cp + (j - 4) * PX);
 #pragma unroll
   for (int i = 0; i < V; ++i) {
-    if (ADJ && SNAP && i + 2 < V) {
-      dinv[i + 2] = Snap<DT>::scaled ? Stask[i + 2] : 1.f;
-      dq[i + 2] = Snap<DT>::ld(Dtask, (size_t)(i + 2) * W4, 1.f);
+    if (ADJ && SNAP && i + kAhead < V) {
+      dinv[i + kAhead] = Snap<DT>::scaled ? Stask[i + kAhead] : 1.f;
+      dq[i + kAhead] = Snap<DT>::ld(Dtask, (size_t)(i + kAhead) * W4, 1.f);
     }
-    if (GW && i + 2 < V) {
-      wq[i + 2] = ld4(wg + (i + 2) * W4);
-      if (ADJ && SNAP) gq[i + 2] = __ldcg(reinterpret_cast<const float4 *>(gg + (i + 2) * W4));
+    if (GW && i + kAhead < V) {
+      wq[i + kAhead] = ld4(wg + (i + kAhead) * W4);
+      if (ADJ && SNAP) gq[i + kAhead] = __ldcg(reinterpret_cast<const float4 *>(gg + (i + kAhead) * W4));
     }
     float *rp = cp + i * PX;
     if (i + 4 < V)
