@@ -4,7 +4,10 @@
 //
 // One CTA owns one (particle, source station) pair for the whole call. It
 // stages the slowness map and an inf-padded travel-time field in shared
-// memory, relaxes the upwind equations in red-black order until nothing
+// memory, the field split by colour into two arrays ((i + j) even / odd, each
+// row holding every other node) so that a warp reading the neighbours of
+// consecutive nodes of one colour reads consecutive words of the other array,
+// relaxes the upwind equations in red-black order until nothing
 // changes (the fixed point is the same discrete solution fast marching
 // reaches in heap order), then each thread traces one ray from a receiver
 // station back to the source and adds its weighted slowness kernel to a
@@ -95,14 +98,22 @@ template <bool GRAD>
 __global__ void __launch_bounds__(kTomoThreads, 6)
 tomo_kernel(TomoArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ny = a.ny, nx = a.nx, n = ny * nx, W = nx + 2, ns = a.ns;
+  const int ny = a.ny, nx = a.nx, n = ny * nx, ns = a.ns;
   const int ks = blockIdx.x % a.nsrc, p = blockIdx.x / a.nsrc;
   const int s = a.slist ? a.slist[ks] : ks;
   const int tid = threadIdx.x;
+  const int Wc = (nx + 3) >> 1;                           // words per row and colour
+  const int PS = (ny + 2) * Wc;
   double *red = (double *)smem_raw;                       // [32]
-  float *Tp = (float *)(smem_raw + 32 * sizeof(double));  // [(ny+2)][(nx+2)]
-  float *F = Tp + (ny + 2) * W;                           // [ny][nx] h / v
+  float *C0 = (float *)(smem_raw + 32 * sizeof(double));  // [(ny+2)][Wc] colour 0
+  float *C1 = C0 + PS;                                    // [(ny+2)][Wc] colour 1
+  float *F = C1 + PS;                                     // [ny][nx] h / v
   float *GY = F + n, *GX = GY + n, *K = GX + n;           // GRAD only
+  // travel time of node (i, j), -1 <= i <= ny, -1 <= j <= nx (the halo is inf)
+  auto T = [&](int i, int j) -> float {
+    const int I = i + 1, J = j + 1;
+    return (((I + J) & 1) ? C1 : C0)[I * Wc + (J >> 1)];
+  };
 
   const float *v = a.V + (size_t)p * n;
   bool bad = false;
@@ -112,12 +123,15 @@ tomo_kernel(TomoArgs a) {
     F[k] = a.h / vk;
     if constexpr (GRAD) K[k] = 0.f;
   }
-  for (int k = tid; k < (ny + 2) * W; k += kTomoThreads) Tp[k] = CUDART_INF_F;
+  for (int k = tid; k < 2 * PS; k += kTomoThreads) C0[k] = CUDART_INF_F;
   if (bad) atomicOr(a.status, 2);
   __syncthreads();
   const int src = a.sta[s];
   const int si = src / nx, sj = src - si * nx;
-  if (tid == 0) Tp[(si + 1) * W + sj + 1] = 0.f;
+  if (tid == 0) {
+    const int I = si + 1, J = sj + 1;
+    (((I + J) & 1) ? C1 : C0)[I * Wc + (J >> 1)] = 0.f;
+  }
   __syncthreads();
 
   // red-black relaxation of the upwind equations from T = inf (monotone:
@@ -125,8 +139,9 @@ tomo_kernel(TomoArgs a) {
   const int half = (n + 1) >> 1;                // colour-0 count bounds colour 1
   int it = 0;
   if (half <= kSlots * kTomoThreads) {
-    // grids up to 2 kSlots x 256 nodes: each thread keeps the padded offsets and
-    // h / v of its nodes in registers for the whole relaxation
+    // grids up to 2 kSlots x 256 nodes: each thread keeps the offsets of its
+    // nodes in their colour array (times two, plus the column parity) and
+    // their h / v in registers for the whole relaxation
     int off[2][kSlots];
     float fv[2][kSlots];
 #pragma unroll
@@ -138,7 +153,8 @@ tomo_kernel(TomoArgs a) {
         off[c][m] = -1;
         fv[c][m] = 0.f;
         if (k < half && colour_node(k, c, ny, nx, i, j)) {
-          off[c][m] = (i + 1) * W + (j + 1);
+          const int I = i + 1, J = j + 1;
+          off[c][m] = ((I * Wc + (J >> 1)) << 1) | (J & 1);
           fv[c][m] = F[i * nx + j];
         }
       }
@@ -146,12 +162,16 @@ tomo_kernel(TomoArgs a) {
       int changed = 0;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
+        float *Tc = c ? C1 : C0;
+        const float *Tn = c ? C0 : C1;
 #pragma unroll
         for (int m = 0; m < kSlots; ++m) {
           if (off[c][m] < 0) continue;
-          float *t = Tp + off[c][m];
-          const float tn = upwind(fminf(t[-1], t[1]), fminf(t[-W], t[W]), fv[c][m]);
-          if (tn < *t) { *t = tn; changed = 1; }
+          const int o = off[c][m] >> 1, pj = off[c][m] & 1;
+          // left, right: the other colour's words o-1+pj, o+pj; up, down: o -/+ Wc
+          const float *q = Tn + o;
+          const float tn = upwind(fminf(q[pj - 1], q[pj]), fminf(q[-Wc], q[Wc]), fv[c][m]);
+          if (tn < Tc[o]) { Tc[o] = tn; changed = 1; }
         }
         if (c == 0) __syncthreads();
       }
@@ -162,12 +182,15 @@ tomo_kernel(TomoArgs a) {
       int changed = 0;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
+        float *Tc = c ? C1 : C0;
+        const float *Tn = c ? C0 : C1;
         for (int k = tid; k < half; k += kTomoThreads) {
           int i, j;
           if (!colour_node(k, c, ny, nx, i, j)) continue;
-          float *t = Tp + (i + 1) * W + (j + 1);
-          const float tn = upwind(fminf(t[-1], t[1]), fminf(t[-W], t[W]), F[i * nx + j]);
-          if (tn < *t) { *t = tn; changed = 1; }
+          const int I = i + 1, J = j + 1, o = I * Wc + (J >> 1), pj = J & 1;
+          const float *q = Tn + o;
+          const float tn = upwind(fminf(q[pj - 1], q[pj]), fminf(q[-Wc], q[Wc]), F[i * nx + j]);
+          if (tn < Tc[o]) { Tc[o] = tn; changed = 1; }
         }
         if (c == 0) __syncthreads();
       }
@@ -182,16 +205,18 @@ tomo_kernel(TomoArgs a) {
     for (int k = tid; k < nr; k += kTomoThreads) {
       const int r = a.sta[s + 1 + k];
       const int ri = r / nx, rj = r - ri * nx;
-      a.Tout[(size_t)p * a.npairs + pbase + k] = Tp[(ri + 1) * W + rj + 1];
+      a.Tout[(size_t)p * a.npairs + pbase + k] = T(ri, rj);
     }
   }
   if constexpr (GRAD) {
     // nodal gradients: central differences inside, one-sided on the edge
     for (int k = tid; k < n; k += kTomoThreads) {
       const int i = k / nx, j = k - i * nx;
-      const float *t = Tp + (i + 1) * W + (j + 1);
-      GX[k] = (j == 0) ? t[1] - t[0] : (j == nx - 1) ? t[0] - t[-1] : 0.5f * (t[1] - t[-1]);
-      GY[k] = (i == 0) ? t[W] - t[0] : (i == ny - 1) ? t[0] - t[-W] : 0.5f * (t[W] - t[-W]);
+      const float t0 = T(i, j);
+      GX[k] = (j == 0) ? T(i, 1) - t0 : (j == nx - 1) ? t0 - T(i, j - 1)
+                                       : 0.5f * (T(i, j + 1) - T(i, j - 1));
+      GY[k] = (i == 0) ? T(1, j) - t0 : (i == ny - 1) ? t0 - T(i - 1, j)
+                                       : 0.5f * (T(i + 1, j) - T(i - 1, j));
     }
     __syncthreads();
 
@@ -200,7 +225,7 @@ tomo_kernel(TomoArgs a) {
       const int r = a.sta[s + 1 + k];
       const int ri = r / nx, rj = r - ri * nx;
       const int pi = pbase + k;
-      const float res = Tp[(ri + 1) * W + rj + 1] - a.dobs[pi];
+      const float res = T(ri, rj) - a.dobs[pi];
       const float sg = a.sigma[pi];
       const float w = res / (sg * sg);
       J += 0.5 * (double)res * (double)res / ((double)sg * (double)sg);
@@ -256,7 +281,8 @@ __global__ void tomo_misfit_kernel(const double *mpart, int P, int nsrc, double 
 
 size_t tomo_smem(int ny, int nx, bool grad) {
   const size_t n = (size_t)ny * nx;
-  return 32 * sizeof(double) + ((size_t)(ny + 2) * (nx + 2) + n * (grad ? 4 : 1)) * sizeof(float);
+  const size_t wc = (size_t)(nx + 3) / 2;
+  return 32 * sizeof(double) + (2 * (size_t)(ny + 2) * wc + n * (grad ? 4 : 1)) * sizeof(float);
 }
 
 }  // namespace
