@@ -418,7 +418,8 @@ typedef struct tomo_ctx tomo_ctx;
 /* stations: host array of n_stations distinct node indices (copied).
  * Errors: VIP_ERR_ARG (ny, nx < 2, h <= 0, fewer than 2 stations, an index
  * outside the grid or repeated), VIP_ERR_UNSUPPORTED (the grid does not fit
- * one CTA's shared memory: (ny + 2)(nx + 2) + 4 ny nx floats), VIP_ERR_CUDA.
+ * one CTA's shared memory: 2 (ny + 2) floor((nx + 3) / 2) + 4 ny nx floats),
+ * VIP_ERR_CUDA.
  * Synchronous. The context is used by one host thread at a time. */
 int  tomo_create(int ny, int nx, double h, int n_stations, const int *stations,
                  tomo_ctx **out);
