@@ -4,12 +4,12 @@
 //
 // One CTA owns one (particle, source station) pair for the whole call. It
 // stages the slowness map and an inf-padded travel-time field in shared
-// memory, the field split by colour into two arrays ((i + j) even / odd, each
-// row holding every other node) so that a warp reading the neighbours of
-// consecutive nodes of one colour reads consecutive words of the other array,
-// relaxes the upwind equations in red-black order until nothing
+// memory and relaxes the upwind equations in red-black order until nothing
 // changes (the fixed point is the same discrete solution fast marching
-// reaches in heap order), then each thread traces one ray from a receiver
+// reaches in heap order). The field is split by colour into two arrays
+// ((i + j) even / odd, each row holding every other node), so a warp reading
+// the neighbours of consecutive nodes of one colour reads consecutive words
+// of the other array. Then each thread traces one ray from a receiver
 // station back to the source and adds its weighted slowness kernel to a
 // shared accumulator, which the CTA finally adds to the particle's gradient.
 //
