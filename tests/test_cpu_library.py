@@ -51,3 +51,21 @@ def test_strerror_and_argument_checks(lib):
     # null arguments
     assert lib.svgd_step(None, None, 1.0, 4, 4, 0.1, 0.0, None, None, 1, None, 0, None, None) == -1
     assert lib.advi_step(None, None, None, 1, None, None, 1.0, 1, 1, None, None, 0.1, None) == -1
+
+
+def test_tomography_argument_checks(lib):
+    # rejected before any device call: too small a grid, a repeated station,
+    # a station outside the grid, fewer than two stations, no context
+    h = ctypes.c_void_p()
+    for ny, nx, st in ((1, 5, [0, 1]), (5, 5, [3, 3]), (5, 5, [0, 25]), (5, 5, [2])):
+        arr = (ctypes.c_int * len(st))(*st)
+        assert lib.tomo_create(ny, nx, 1.0, len(st), arr, ctypes.byref(h)) == -1
+        assert not h.value
+    arr = (ctypes.c_int * 2)(0, 1)
+    assert lib.tomo_create(5, 5, 0.0, 2, arr, ctypes.byref(h)) == -1
+    assert lib.tomo_pair_count(None) == -1
+    assert lib.tomo_traveltimes(None, None, 1, None, None) == -1
+    assert lib.tomo_gradient(None, None, 1, None, None, None, None, None, None) == -1
+    assert lib.tomo_gradient_sources(None, None, 1, None, None, None, 1, None, None,
+                                     None) == -1
+    assert lib.tomo_destroy(None) == 0
