@@ -195,3 +195,21 @@ def test_source_minibatches_partition_the_misfit_and_gradient():
     Jm = np.mean([tomo.misfit_gradient(v, cfg.h, sta, d, sig, sources=list(c))[0]
                   for c in subsets]) * S / nb
     assert Jm == pytest.approx(J, rel=1e-12)
+
+
+def test_rays_converge_to_the_circular_ray_of_a_constant_gradient_medium():
+    # in v = v0 + g y every ray is a circular arc centred at depth -v0/g;
+    # two surface stations 40 km apart: radius sqrt(20^2 + (v0/g)^2)
+    v0, g = 2.0, 0.05
+    cx, cy = 40.0, -v0 / g
+    R = np.hypot(20.0, cy)
+    rms = []
+    for N, h in ((41, 2.0), (81, 1.0), (161, 0.5)):
+        v = np.repeat((v0 + g * np.arange(N) * h)[:, None], N, axis=1)
+        src, rcv = (0, int(20 / h)), (0, int(60 / h))
+        segs = tomo.trace_ray(tomo.fast_marching(v, h, src), src, rcv)
+        pts = np.array([p for p, q in segs] + [segs[-1][1]]) * h
+        d = np.hypot(pts[:, 1] - cx, pts[:, 0] - cy) - R
+        rms.append(np.sqrt(np.mean(d * d)))
+        assert pts[:, 0].max() < R + cy + 0.5        # never below the true turning depth
+    assert rms[0] > rms[1] > rms[2] and rms[2] < 0.5
