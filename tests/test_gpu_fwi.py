@@ -158,7 +158,13 @@ def test_autograd_backward_is_the_oracle_adjoint():
         assert rel(got[p], ref[p]) <= 5e-5, rel(got[p], ref[p])
 
 
-@pytest.mark.parametrize("prec,bound", [(vg.FWI_CKPT_BF16, 2e-2), (vg.FWI_CKPT_FP16, 5e-3)])
+# The imaging condition sums products mu^k D^k in which only the stored D^k is
+# rounded to the snapshot format, each by at most its unit roundoff: the
+# relative error of the gradient is at most that unit roundoff, 2^-9 for BF16
+# and 2^-11 for FP16 (its per-block power-of-two scale keeps the values normal).
+# Measured on the 64x64 case: 1.7e-4 (BF16) and 2.1e-5 (FP16).
+@pytest.mark.parametrize("prec,bound", [(vg.FWI_CKPT_BF16, 2.0 ** -9),
+                                        (vg.FWI_CKPT_FP16, 2.0 ** -11)])
 def test_reduced_precision_snapshots_error_is_bounded(prec, bound):
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
     J_ref, G_ref = cfg1_oracle_gradients(2)
