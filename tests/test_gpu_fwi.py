@@ -159,10 +159,11 @@ def test_autograd_backward_is_the_oracle_adjoint():
 
 
 # The imaging condition sums products mu^k D^k in which only the stored D^k is
-# rounded to the snapshot format, each by at most its unit roundoff: the
-# relative error of the gradient is at most that unit roundoff, 2^-9 for BF16
-# and 2^-11 for FP16 (its per-block power-of-two scale keeps the values normal).
-# Measured on the 64x64 case: 1.7e-4 (BF16) and 2.1e-5 (FP16).
+# rounded to the snapshot format, each by at most its unit roundoff u (2^-9 for
+# BF16, 2^-11 for FP16, whose per-block power-of-two scale keeps the values
+# normal), so the error is at most u times the sum of the terms' magnitudes.
+# The bound is u itself, which holds while the time sum does not cancel by more
+# than the margin; measured on the 64x64 case: 1.7e-4 (BF16), 2.1e-5 (FP16).
 @pytest.mark.parametrize("prec,bound", [(vg.FWI_CKPT_BF16, 2.0 ** -9),
                                         (vg.FWI_CKPT_FP16, 2.0 ** -11)])
 def test_reduced_precision_snapshots_error_is_bounded(prec, bound):
