@@ -73,11 +73,17 @@ def parse():
                     help="override the number of time steps (profiling cases only)")
     ap.add_argument("--tomo-method", default="svgd", choices=["svgd", "ssvgd", "advi"],
                     help="update of the tomography workload")
-    ap.add_argument("--workload", default="svgd", choices=["svgd", "ssvgd", "advi", "tomo"],
+    ap.add_argument("--workload", default="svgd",
+                    choices=["svgd", "ssvgd", "advi", "tomo", "update"],
                     help="svgd: the batched SVGD step (default); ssvgd / advi: the "
                          "240x600, 40-source shape with the stochastic-SVGD or "
                          "mean-field ADVI update; tomo: the travel-time tomography "
-                         "SVGD iteration")
+                         "SVGD iteration; update: svgd_step / ssvgd_step alone on "
+                         "--particles x --dim random particles")
+    ap.add_argument("--dim", type=int, default=36000,
+                    help="coordinates per particle of the update workload")
+    ap.add_argument("--stochastic", action="store_true",
+                    help="update workload: ssvgd_step with injected noise")
     return ap.parse_args()
 
 
@@ -740,6 +746,51 @@ def run_tomo(args, torch):
     print(json.dumps(line))
 
 
+def run_update(args, torch):
+    """svgd_step or ssvgd_step (injected unit-normal noise) alone on seeded
+    standard-normal particles and gradients [--particles, --dim], three-piece
+    BF16 Gram and the tensor-core update: milliseconds per call."""
+    import paper_2310_13325_gb300 as vg
+    from paper_2310_13325_gb300 import build as vbuild
+    vbuild.build()
+    n, d = args.particles or 600, args.dim
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(7)
+    X0 = torch.tensor(rng.standard_normal((n, d)).astype(np.float32), device=dev)
+    G = torch.tensor(rng.standard_normal((n, d)).astype(np.float32), device=dev)
+    xi = torch.tensor(rng.standard_normal((n, d)).astype(np.float32), device=dev)
+    gram = vg.VIP_GRAM_BF16X3
+    ws = torch.empty(vg.svgd_workspace_size(n, d, gram, args.stochastic), dtype=torch.uint8,
+                     device=dev)
+    X = X0.clone()
+
+    def call():
+        X.copy_(X0)
+        if args.stochastic:
+            vg.ssvgd_step(X, G, 1e-3, seed=3, it=1, xi=xi, gram_precision=gram, ws=ws)
+        else:
+            vg.svgd_step(X, G, 1e-3, gram_precision=gram, ws=ws)
+
+    for _ in range(max(args.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        call()
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    print(json.dumps({"metric": "%s time" % ("ssvgd_step" if args.stochastic else "svgd_step"),
+                      "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+                      "warmup": max(args.warmup, 3), "ms_per_step": ms,
+                      "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "%d particles x %d coordinates, three-piece BF16 "
+                                             "Gram, tensor-core update" % (n, d)}}))
+
+
 def reduce_over_ranks(t_ms, e2e_ms, device):
     """Slowest rank's step time and end-to-end time (max over ranks). Every
     rank runs an independent replica; no data crosses ranks."""
@@ -768,6 +819,9 @@ def main():
     import torch
     if args.workload == "tomo":
         run_tomo(args, torch)
+        return
+    if args.workload == "update":
+        run_update(args, torch)
         return
     if args.workload != "svgd":
         run_other_workload(args, torch)
