@@ -207,11 +207,15 @@ def fold(grad_pad, geom):
     return out
 
 
-def pair_gradient(v, geom, isrc, resid_fn, both_forms=False):
+def pair_gradient(v, geom, isrc, resid_fn, both_forms=False, magnitude=False):
     """Velocity gradient (physical grid) for one source.
 
     resid_fn(traces) -> dJ/dtraces [R, nt]. Returns (traces, grad[nz, nx]) and,
-    if both_forms, also the two padded-grid gradients for comparison."""
+    if both_forms, also the two padded-grid gradients for comparison. With
+    magnitude, returns (traces, grad, mag) where mag[nz, nx] is the same sum
+    with every time term replaced by its absolute value,
+    2 vpad dt^2 sum_n |g lambda^{n+1} (L a^n + s^n)|, folded: the scale
+    against which the rounding of one factor of each term is measured."""
     src = (geom.src_iz[isrc], geom.src_ix[isrc])
     q = source_function(geom)
     traces, hist = propagate(v, geom, src, q, keep=True)
@@ -223,15 +227,21 @@ def pair_gradient(v, geom, isrc, resid_fn, both_forms=False):
     # hist[j] = a^{j-1}
     acc1 = np.zeros_like(vpad)
     acc2 = np.zeros_like(vpad)
+    accm = np.zeros_like(vpad)
     for n in range(geom.nt):
         a_nm1, a_n, a_np1 = hist[n], hist[n + 1], hist[n + 2]
         src_term = laplacian(a_n, geom.dx)
         src_term[sz, sx] += q[n]
-        acc1 += g * lam[n + 1] * src_term
+        term = g * lam[n + 1] * src_term
+        acc1 += term
+        if magnitude:
+            accm += np.abs(term)
         if both_forms:
             acc2 += lam[n + 1] * (a_np1 - 2.0 * g * a_n + g * g * a_nm1)
     gpad1 = 2.0 * vpad * geom.dt ** 2 * acc1
     grad = fold(gpad1, geom)
+    if magnitude:
+        return traces, grad, fold(2.0 * vpad * geom.dt ** 2 * accm, geom)
     if both_forms:
         gpad2 = 2.0 / vpad * acc2
         return traces, grad, gpad1, gpad2
@@ -255,6 +265,21 @@ def gradient(v, geom, d_obs, sigma, sources=None):
         J += misfit(tr, d_obs[s], sigma)
         grad += gs
     return J, grad
+
+
+def gradient_magnitude(v, geom, d_obs, sigma, sources=None):
+    """Per physical cell, the sum over sources and time steps of the absolute
+    values of the imaging-condition terms whose signed sum is dJ/dv (see
+    pair_gradient): rounding one factor of every term to a relative
+    precision u changes dJ/dv by at most u times this. Returns [nz, nx]."""
+    v = np.asarray(v, dtype=np.float64).reshape(geom.nz, geom.nx)
+    mag = np.zeros((geom.nz, geom.nx))
+    for s in (range(geom.nsrc) if sources is None else sources):
+        def resid_fn(tr, s=s):
+            return (tr - d_obs[s]) / sigma ** 2
+        _, _, m = pair_gradient(v, geom, s, resid_fn, magnitude=True)
+        mag += m
+    return mag
 
 
 def gradients(V, geom, d_obs, sigma, sources=None):

@@ -26,15 +26,21 @@ Particles X [n, d], gradients G [n, d] = grad log p(m_j | d_obs).
 import numpy as np
 
 
+def sqdist_rows(X, rows):
+    """D2[rows, :] with D2[i, j] = sum_c (X[i, c] - X[j, c])^2, taken directly."""
+    X = np.asarray(X, dtype=np.float64)
+    rows = list(rows)
+    D2 = np.zeros((len(rows), X.shape[0]))
+    for k, i in enumerate(rows):
+        diff = X - X[i][None, :]
+        D2[k] = np.einsum("jc,jc->j", diff, diff)
+    return D2
+
+
 def pairwise_sqdist(X):
     """D2[i, j] = sum_c (X[i, c] - X[j, c])^2, taken directly."""
     X = np.asarray(X, dtype=np.float64)
-    n = X.shape[0]
-    D2 = np.zeros((n, n))
-    for i in range(n):
-        diff = X - X[i][None, :]
-        D2[i] = np.einsum("jc,jc->j", diff, diff)
-    return D2
+    return sqdist_rows(X, range(X.shape[0]))
 
 
 def median_bandwidth(D2):
@@ -65,6 +71,48 @@ def svgd_direction(X, G, h2=None):
     for i in range(n):                    # sum_j k(m_j, m_i) (m_i - m_j) / h^2
         repulse[i] = (K[i][:, None] * (X[i][None, :] - X)).sum(axis=0) / h2
     return (attract + repulse) / n, h2, K
+
+
+def svgd_direction_rows(X, G, rows, D2, h2=None):
+    """phi(m_i) of Eq. (17) for the particles i in rows only, given the full
+    squared-distance matrix D2 (pairwise_sqdist): the same sums over j as
+    svgd_direction, evaluated for those i. Returns (phi [len(rows), d], h2, K)."""
+    X = np.asarray(X, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    n = X.shape[0]
+    if h2 is None or h2 <= 0:
+        h2 = median_bandwidth(D2)
+    K = rbf(D2, h2)
+    phi = np.zeros((len(rows), X.shape[1]))
+    for k, i in enumerate(rows):
+        attract = K[i] @ G                                   # sum_j k(m_j, m_i) G_j
+        repulse = (K[i][:, None] * (X[i][None, :] - X)).sum(axis=0) / h2
+        phi[k] = (attract + repulse) / n
+    return phi, h2, K
+
+
+def svgd_step_rows(X, G, eps, rows, D2, h2=None, lo=None, hi=None):
+    """Rows of svgd_step: the updated particles i in rows."""
+    X = np.asarray(X, dtype=np.float64)
+    phi, h2u, _ = svgd_direction_rows(X, G, rows, D2, h2)
+    lo_ = None if lo is None else np.asarray(lo, dtype=np.float64).reshape(-1)
+    hi_ = None if hi is None else np.asarray(hi, dtype=np.float64).reshape(-1)
+    return clip(X[list(rows)] + eps * phi, lo_, hi_), h2u
+
+
+def ssvgd_step_rows(X, G, eps, xi, rows, D2, h2=None, lo=None, hi=None):
+    """Rows of ssvgd_step: the updated particles i in rows, with the noise
+    sqrt(2 eps / n) (Lk xi)_i of Eq. (25) (Lk from the full kernel matrix).
+    Returns (X_new[rows], h2, tau)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    phi, h2u, K = svgd_direction_rows(X, G, rows, D2, h2)
+    L, tau = jittered_cholesky(K)
+    xi = np.asarray(xi, dtype=np.float64)
+    noise = np.sqrt(2.0 * eps / n) * np.stack([L[i] @ xi for i in rows])
+    lo_ = None if lo is None else np.asarray(lo, dtype=np.float64).reshape(-1)
+    hi_ = None if hi is None else np.asarray(hi, dtype=np.float64).reshape(-1)
+    return clip(X[list(rows)] + eps * phi + noise, lo_, hi_), h2u, tau
 
 
 def clip(X, lo, hi):

@@ -209,3 +209,26 @@ def test_source_minibatch_sums_and_unbiased_scaling():
     Gm = np.mean([(4 / nb) * sum(per[s][1] for s in B) for B in subsets], axis=0)
     assert np.isclose(Jm, J, rtol=1e-12)
     assert np.allclose(Gm, G, rtol=1e-10, atol=1e-12 * np.abs(G).max())
+
+
+def test_gradient_magnitude_bounds_and_symmetries():
+    """The per-cell sum of the imaging terms' magnitudes: it bounds |dJ/dv|
+    (triangle inequality) and the sum of the per-source magnitudes is the
+    magnitude over all sources; flipping the sign of the adjoint source flips
+    the gradient but leaves the magnitude unchanged (each term is linear in
+    the adjoint field), and scaling sigma by 2 scales both by 1/4."""
+    g, _, d_obs, sigma, v0 = _problem()
+    J, G = fwi.gradient(v0, g, d_obs, sigma)
+    M = fwi.gradient_magnitude(v0, g, d_obs, sigma)
+    assert np.all(M >= np.abs(G) * (1 - 1e-12))
+    assert M.sum() > 1.01 * np.abs(G).sum()          # the time sum cancels
+    parts = sum(fwi.gradient_magnitude(v0, g, d_obs, sigma, sources=[s])
+                for s in range(g.nsrc))
+    assert np.allclose(parts, M, rtol=1e-12, atol=0)
+    f = lambda tr: (tr - d_obs[0]) / sigma ** 2
+    _, g1, m1 = fwi.pair_gradient(v0, g, 0, f, magnitude=True)
+    _, g2, m2 = fwi.pair_gradient(v0, g, 0, lambda tr: -f(tr), magnitude=True)
+    assert np.allclose(g2, -g1, rtol=1e-12, atol=0)
+    assert np.allclose(m2, m1, rtol=1e-12, atol=0)
+    M2 = fwi.gradient_magnitude(v0, g, d_obs, 2 * sigma)
+    assert np.allclose(M2, M / 4, rtol=1e-12, atol=0)

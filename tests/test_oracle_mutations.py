@@ -31,7 +31,8 @@ FWI = [
     ("taper_profile", "into = np.maximum(np.maximum(nb - i, i - (N - 1 - nb)), 0)",
      "into = np.maximum(np.maximum(nb - i - 1, i - (N - 1 - nb)), 0)"),
     ("adjoint_taper", "- g * g * lam2 + rho", "- g * lam2 + rho"),
-    ("imaging_taper", "acc1 += g * lam[n + 1] * src_term", "acc1 += lam[n + 1] * src_term"),
+    ("imaging_taper", "term = g * lam[n + 1] * src_term", "term = lam[n + 1] * src_term"),
+    ("magnitude_abs", "accm += np.abs(term)", "accm += term"),
 ]
 SVGD = [
     ("bandwidth_log", "return med / (2.0 * np.log(n + 1.0))", "return med / (2.0 * np.log(n))"),
@@ -46,6 +47,9 @@ SVGD = [
 SSVGD_NOISE = ("noise = np.sqrt(2.0 * eps / n) * (L @ np.asarray(xi, dtype=np.float64))\n"
                "    return clip(X + eps * phi + noise, lo, hi), h2u, tau")
 SVGD += [
+    ("rows_noise_transposed", "np.stack([L[i] @ xi for i in rows])",
+     "np.stack([L[:, i] @ xi for i in rows])"),
+    ("rows_attraction_shift", "attract = K[i] @ G ", "attract = K[i][:-1] @ G[1:] "),
     ("noise_scale", SSVGD_NOISE, SSVGD_NOISE.replace("np.sqrt(2.0 * eps / n)", "np.sqrt(eps / n)")),
     ("noise_transposed", SSVGD_NOISE, SSVGD_NOISE.replace("(L @", "(L.T @")),
 ]

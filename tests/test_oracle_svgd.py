@@ -301,3 +301,28 @@ def test_unconstrained_single_particle_uniform_target_reaches_mode():
         th, _ = svgd.svgd_step_unconstrained(th, np.zeros_like(th), 0.5, a, b)
     assert np.allclose(th, 0.0, atol=1e-8)
     assert np.allclose(svgd.to_model(th, a, b), (a + b) / 2, rtol=1e-10)
+
+
+def test_row_restricted_updates_equal_the_full_ones():
+    """svgd_step_rows / ssvgd_step_rows evaluate the same sums as svgd_step /
+    ssvgd_step for a subset of the particles (used where the full update of
+    every particle is too slow for the oracle)."""
+    rng = np.random.default_rng(21)
+    n, d = 9, 40
+    X = rng.standard_normal((n, d))
+    G = rng.standard_normal((n, d))
+    xi = rng.standard_normal((n, d))
+    lo, hi = -np.full(d, 1.5), np.full(d, 1.5)
+    rows = [0, 4, 8]
+    D2 = svgd.pairwise_sqdist(X)
+    brute = np.array([[((X[i] - X[j]) ** 2).sum() for j in range(n)] for i in range(n)])
+    assert np.allclose(D2, brute, rtol=1e-14, atol=0)
+    assert np.allclose(svgd.sqdist_rows(X, rows), brute[rows], rtol=1e-14, atol=0)
+    full, h2 = svgd.svgd_step(X, G, 0.3, lo=lo, hi=hi)
+    part, h2r = svgd.svgd_step_rows(X, G, 0.3, rows, D2, lo=lo, hi=hi)
+    assert h2r == h2
+    assert np.allclose(part, full[rows], rtol=1e-13, atol=1e-14)
+    fulls, h2s, tau = svgd.ssvgd_step(X, G, 0.3, xi, lo=lo, hi=hi)
+    parts, h2sr, taur = svgd.ssvgd_step_rows(X, G, 0.3, xi, rows, D2, lo=lo, hi=hi)
+    assert taur == tau and h2sr == h2s
+    assert np.allclose(parts, fulls[rows], rtol=1e-13, atol=1e-14)
