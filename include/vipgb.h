@@ -37,6 +37,7 @@ typedef struct CUstream_st *vip_stream_t; /* same type as cudaStream_t */
 #define VIP_ERR_TIMEOUT  -5  /* a bounded device-side wait gave up          */
 #define VIP_ERR_NOTPD    -6  /* kernel matrix not positive definite          */
 #define VIP_ERR_UNSUPPORTED -7 /* no feasible launch plan on this device      */
+#define VIP_ERR_NONFINITE -8 /* a NaN or infinity among the inputs          */
 
 const char *vip_strerror(int code);
 
@@ -146,9 +147,18 @@ int  fwi_set_autotune(fwi_ctx *ctx, int enable);
  * (host): {cluster_ctas, rows_per_thread, threads, band_rows, concurrent
  * pairs, ckpt_every, work_items, sources_per_item, coeff (1 shared, 2
  * global memory), shared-memory bytes per CTA}, and the device bytes the
- * context holds after planning to bytes_out (host, may be NULL). */
+ * context holds after planning to bytes_out (host, may be NULL). When no
+ * plan fits the workspace limit it returns VIP_ERR_NOMEM and writes to
+ * bytes_out the smallest scratch any plan tried would need (the limit a
+ * caller would have to grant at the current checkpoint setting). */
 int  fwi_query_plan(fwi_ctx *ctx, int P, int precision, int *plan_out,
                     size_t *bytes_out);
+
+/* Device scratch bytes the last planned call on this context needed, or, if
+ * that call returned VIP_ERR_NOMEM, the smallest footprint it tried and
+ * could not fit under the workspace limit (host, synchronous, no device
+ * call). 0 before the first call. */
+size_t fwi_bytes_needed(fwi_ctx *ctx);
 
 /* Seismograms for P models.
  *   v    [P][nz][nx] velocities (m/s)
@@ -189,9 +199,11 @@ int  fwi_adjoint(fwi_ctx *ctx, const float *v, int P, const float *dseis,
                  float *grad, int precision, vip_stream_t stream);
 
 /* Device-side status of the last call on this context (synchronises the
- * stream it last used): VIP_OK, VIP_ERR_CFL if some model violated
- * max(v) dt/dx <= 0.5547 (the 2-D stability bound of the 8th-order
- * leapfrog scheme), in which case the outputs of that call are undefined. */
+ * stream it last used): VIP_OK; VIP_ERR_NONFINITE if some velocity was NaN
+ * or infinite, or a misfit came out non-finite (e.g. NaN observed data);
+ * otherwise VIP_ERR_CFL if some model violated max(v) dt/dx <= 0.5547 (the
+ * 2-D stability bound of the 8th-order leapfrog scheme). After either error
+ * the outputs of that call are undefined. */
 int  fwi_last_status(fwi_ctx *ctx);
 
 /* ======================================================================
@@ -220,6 +232,21 @@ int  fwi_last_status(fwi_ctx *ctx);
 #define VIP_GRAM_FP32    2  /* SIMT FP32 Gram without tensor cores (reference) */
 
 size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic);
+
+/* Device-side status of the last svgd_step / ssvgd_step / svgd_step_q /
+ * ssvgd_step_q / svgd_sqdist that used the workspace ws (its first 16 bytes
+ * hold the status words; synchronises stream):
+ *   VIP_OK
+ *   VIP_ERR_TIMEOUT    a bounded wait inside a tensor-core kernel expired
+ *                      (the Gram: h2_used is NaN and so are the particles;
+ *                      the update: every particle is set to NaN)
+ *   VIP_ERR_NONFINITE  X or G held a NaN or infinity. With the tensor-core
+ *                      update (VIP_GRAM_BF16, VIP_GRAM_BF16X3) the particles
+ *                      are left unchanged; with the FP32 reference update
+ *                      they are undefined.
+ * Errors of its own: VIP_ERR_ARG (ws NULL or not 256-byte aligned),
+ * VIP_ERR_CUDA. */
+int  svgd_status(const void *ws, vip_stream_t stream);
 
 /* Rows a9-a10 of one step on their own: the centred Gram on the tensor cores
  * (or SIMT), the squared distances D2 [n][n] (device, FP64, zero diagonal,
@@ -460,6 +487,23 @@ int  tomo_gradient_sources(tomo_ctx *ctx, const float *V, int P, const float *do
  * if a travel-time field did not settle within ny * nx relaxation sweeps;
  * the outputs of that call are then undefined. */
 int  tomo_last_status(tomo_ctx *ctx);
+
+/* ======================================================================
+ * Test hook (no counterpart in the paper)
+ *
+ * Every wait on an mbarrier inside the tensor-core kernels (the Gram and the
+ * update of svgd_step / ssvgd_step) is bounded: when the bound expires the
+ * kernel records the failure in its status word, waits (bounded) for the
+ * copies it has issued, frees its tensor memory and returns, so the CUDA
+ * context stays usable and svgd_status() reports VIP_ERR_TIMEOUT.
+ * vip_test_set_wait sets, for the launches that follow in this process, the
+ * bound in SM clock cycles (0 restores the default of 2e9, about one second)
+ * and, with stall_producer = 1, stops the copy producer of those kernels
+ * from issuing anything, so that the consumer's wait expires by design
+ * (tests of the error path; nothing faults). Not thread-safe; reset with
+ * vip_test_set_wait(0, 0). Errors: VIP_ERR_ARG (negative cycles,
+ * stall_producer not 0 or 1). Host only, synchronous. */
+int  vip_test_set_wait(long long cycles, int stall_producer);
 
 #ifdef __cplusplus
 }

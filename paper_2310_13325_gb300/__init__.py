@@ -23,6 +23,8 @@ from . import _lib
 from ._lib import FwiGeom, VipError, check
 
 FWI_FP32, FWI_CKPT_BF16, FWI_CKPT_FP16 = 0, 1, 2
+VIP_OK, VIP_ERR_ARG, VIP_ERR_CFL, VIP_ERR_NOMEM, VIP_ERR_CUDA = 0, -1, -2, -3, -4
+VIP_ERR_TIMEOUT, VIP_ERR_NOTPD, VIP_ERR_UNSUPPORTED, VIP_ERR_NONFINITE = -5, -6, -7, -8
 FWI_MODE_BATCHED, FWI_MODE_PLAIN = 0, 1
 VIP_GRAM_BF16, VIP_GRAM_BF16X3, VIP_GRAM_FP32 = 0, 1, 2
 
@@ -31,7 +33,9 @@ __all__ = ["Fwi", "FwiSeis", "Tomo", "svgd_step", "ssvgd_step", "svgd_inverse_va
            "ASCENT_SGD", "ASCENT_ADAGRAD", "ASCENT_ADADELTA", "ASCENT_ADAM", "advi_sample", "advi_step",
            "philox_normal", "svgd_workspace_size", "svgd_sqdist", "svgd_step_noalloc", "FWI_FP32", "FWI_CKPT_BF16",
            "FWI_CKPT_FP16", "FWI_MODE_BATCHED", "FWI_MODE_PLAIN", "VIP_GRAM_BF16",
-           "VIP_GRAM_BF16X3", "VIP_GRAM_FP32", "VipError"]
+           "VIP_GRAM_BF16X3", "VIP_GRAM_FP32", "VipError", "svgd_status", "VIP_OK",
+           "VIP_ERR_ARG", "VIP_ERR_CFL", "VIP_ERR_NOMEM", "VIP_ERR_CUDA", "VIP_ERR_TIMEOUT",
+           "VIP_ERR_NOTPD", "VIP_ERR_UNSUPPORTED", "VIP_ERR_NONFINITE"]
 
 
 def _torch():
@@ -125,6 +129,11 @@ class Fwi:
 
     def last_status(self):
         return self._L.fwi_last_status(self._h)
+
+    def bytes_needed(self):
+        """Device scratch bytes the last planned call needed (or, after
+        VIP_ERR_NOMEM, the smallest footprint it could not fit)."""
+        return int(self._L.fwi_bytes_needed(self._h))
 
     def _models(self, v):
         """Accept one model [nz, nx] or a batch [P, nz, nx] / [P, nz*nx]."""
@@ -369,6 +378,12 @@ def svgd_step(X, G, eps, h2=0.0, lo=None, hi=None, gram_precision=VIP_GRAM_BF16X
                                       float(gscale), _ptr(q, torch.float32, "q"), *common),
               "svgd_step_q")
     return ws, h2_used
+
+
+def svgd_status(ws, stream=None):
+    """Status of the last SVGD call that used the workspace ws (synchronises
+    the stream): VIP_OK, VIP_ERR_TIMEOUT or VIP_ERR_NONFINITE."""
+    return int(_lib.load().svgd_status(_ptr(ws), _stream(stream)))
 
 
 def svgd_inverse_variance(X, out=None, stream=None):

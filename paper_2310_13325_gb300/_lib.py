@@ -42,6 +42,9 @@ _SIGS = {
     "fwi_adjoint": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int,
                             c_void_p]),
     "fwi_last_status": (c_int, [c_void_p]),
+    "fwi_bytes_needed": (c_size_t, [c_void_p]),
+    "svgd_status": (c_int, [c_void_p, c_void_p]),
+    "vip_test_set_wait": (c_int, [ctypes.c_longlong, c_int]),
     "svgd_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int]),
     "svgd_sqdist": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                             c_size_t, c_void_p]),

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <set>
 #include <tuple>
 #include <vector>
 
@@ -55,8 +56,9 @@ struct Tables {
   int rmax = 0;   // largest number of receivers in one band
 };
 
+constexpr int kGraphKeyLen = 17;
 struct GraphEntry {
-  std::array<uintptr_t, 13> key;
+  std::array<uintptr_t, kGraphKeyLen> key;
   cudaGraphExec_t exec;
 };
 
@@ -81,9 +83,11 @@ struct fwi_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   std::map<std::tuple<int, int, int>, std::array<int, 4>> tuned;   // (P, mode*16+dtype, S) -> Q,V,T,gw
+  std::set<std::tuple<int, int, int>> untunable;   // keys whose trials all exceeded the budget
   int force_Q = 0, force_V = 0, force_T = 0, force_spi = 0;          // launch override
   int force_coeff = 0;   // 0 any, 1 coefficients in shared memory, 2 in global memory
   int use_graphs = 1;   // VIPGB_GRAPHS=0 in the environment: eager launches
+  size_t need_bytes = 0;   // device bytes the last planned call needs (or lacked)
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
   int *pl_recmap = nullptr;
@@ -231,6 +235,22 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
                    (size_t)pl.ncl * pl.slot_bytes;
 }
 
+// Launch attributes of a wave kernel: the dynamic shared-memory cap is set to
+// the most the device allows (less the kernel's static shared memory) and
+// clusters beyond 8 CTAs are allowed, once and to the same values whatever the
+// plan. A launch then carries its own dynamic size, and nothing a later plan
+// or candidate enumeration does can change what a captured graph's kernel node
+// was instantiated with.
+static int set_wave_attrs(fwi_ctx *c, const void *fn) {
+  cudaFuncAttributes fa;
+  VIP_TRY(cudaFuncGetAttributes(&fa, fn));
+  const int cap = (int)(c->smem_optin - fa.sharedSizeBytes);
+  if (fa.maxDynamicSharedSizeBytes != cap)
+    VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  return VIP_OK;
+}
+
 static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<Plan> &out) {
   const bool grad = mode != WM_FORWARD;
   const int Vs[4] = {4, 5, 8, 10};
@@ -242,6 +262,7 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
     if (!fn) continue;
     cudaFuncAttributes fa;
     VIP_TRY(cudaFuncGetAttributes(&fa, fn));
+    if (int rc = set_wave_attrs(c, fn)) return rc;
     for (int Q = 1; Q <= 16; ++Q) {
       const int Hb = band_height(c->NZ, Q, V);
       if ((Q - 1) * Hb >= c->NZ) continue;
@@ -268,8 +289,6 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
         pl.Q = Q; pl.V = V; pl.T = T; pl.Hb = Hb; pl.NXg = NXg; pl.PX = PX;
         pl.ntask = ntask; pl.ntask_pad = ntask_pad; pl.nwblk = ntask_pad / 32;
         pl.smem = smem; pl.mode = mode; pl.dtype = dtype; pl.gw = gw;
-        VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (Q > 8) VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(Q, 1, 1);
         cfg.blockDim = dim3(T, 1, 1);
@@ -328,6 +347,7 @@ static int make_candidates(fwi_ctx *c, int P, int mode, int dtype, std::vector<P
 // Choose K and ncl under the memory budget.
 static int fit_memory(fwi_ctx *c, Plan &pl, int P) {
   const size_t budget = free_budget(c);
+  size_t least = (size_t)-1;   // smallest footprint tried
   std::vector<int> Ks;
   if (pl.mode == WM_FORWARD) Ks = {1};
   else if (c->ckpt >= 1) Ks = {std::min(c->ckpt, c->N)};
@@ -338,10 +358,14 @@ static int fit_memory(fwi_ctx *c, Plan &pl, int P) {
       Plan t = pl;
       t.ncl = ncl;
       plan_memory(c, t, P);
-      if (t.total_bytes <= budget) { pl = t; return VIP_OK; }
+      least = std::min(least, t.total_bytes);
+      if (t.total_bytes <= budget) { c->need_bytes = t.total_bytes; pl = t; return VIP_OK; }
       if (c->ckpt == 0 && ncl < pl.ncl / 2) break;   // prefer a larger K over idling SMs
     }
   }
+  // the smallest footprint among the plans tried (one cluster for the
+  // interval(s) allowed): what the caller would have to grant
+  c->need_bytes = least;
   return VIP_ERR_NOMEM;
 }
 
@@ -375,10 +399,16 @@ static int choose_plan(fwi_ctx *c, int P, int mode, int dtype, Plan &out) {
   return fit_memory(c, out, P);
 }
 
-static int ensure_scratch(fwi_ctx *c, size_t bytes) {
-  if (bytes <= c->scratch_bytes) return VIP_OK;
+// Drop every cached graph (their launches may no longer be what a call with
+// the current settings would enqueue).
+static void drop_graphs(fwi_ctx *c) {
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
+}
+
+static int ensure_scratch(fwi_ctx *c, size_t bytes) {
+  if (bytes <= c->scratch_bytes) return VIP_OK;
+  drop_graphs(c);
   if (c->scratch) {
     VIP_TRY(cudaDeviceSynchronize());
     VIP_TRY(cudaFree(c->scratch));
@@ -405,13 +435,15 @@ __global__ void grad_merge_kernel(const float *GI, int P, int ipp, int d, float 
 }
 
 __global__ void j_reduce_kernel(const double *Jpart, int P, int S, int Q, double scale,
-                                double *misfit) {
+                                double *misfit, int *status) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double t = 0.0;
   for (int s = 0; s < S; ++s)
     for (int b = 0; b < Q; ++b) t += Jpart[((size_t)p * S + s) * Q + b];
   misfit[p] = t * scale;
+  // a non-finite misfit (non-finite observed data or wavefield) is reported
+  if (!isfinite(t)) atomicOr(status, 4);
 }
 
 static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams &wp) {
@@ -461,12 +493,10 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   return cv.ok() ? VIP_OK : VIP_ERR_NOMEM;
 }
 
-static int prepare_wave(const Plan &pl) {
+static int prepare_wave(fwi_ctx *c, const Plan &pl) {
   const void *fn = kernel_ptr(pl.V, pl.mode, pl.dtype, pl.gw);
   if (!fn) return VIP_ERR_UNSUPPORTED;
-  VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-  if (pl.Q > 8) VIP_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  return VIP_OK;
+  return set_wave_attrs(c, fn);
 }
 
 static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream_t st) {
@@ -502,7 +532,8 @@ static int enqueue_batched(fwi_ctx *c, const Plan &pl, WaveParams &wp, int P, do
   }
   if (pl.mode == WM_GRADIENT && misfit) {
     const double scale = 0.5 / (sigma * sigma);
-    j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(wp.Jpart, P, c->S, pl.Q, scale, misfit);
+    j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(wp.Jpart, P, c->S, pl.Q, scale, misfit,
+                                                     c->d_status);
     VIP_CHECK_LAUNCH();
   }
   return VIP_OK;
@@ -514,9 +545,11 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
 static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float *dobs,
                        const float *dseis, double sigma, double *misfit, float *grad,
                        float *seis, int dtype, cudaStream_t st) {
-  if (c->autotune && !c->tuned.count(std::make_tuple(P, mode * 16 + dtype, c->S))) {
+  const auto tkey = std::make_tuple(P, mode * 16 + dtype, c->S);
+  if (c->autotune && !c->tuned.count(tkey) && !c->untunable.count(tkey)) {
     int rc = autotune_plan(c, P, mode, dtype, v, dobs, dseis, sigma, st);
     if (rc) return rc;
+    if (!c->tuned.count(tkey)) c->untunable.insert(tkey);
   }
   Plan pl;
   int rc = choose_plan(c, P, mode, dtype, pl);
@@ -534,15 +567,19 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
   // graph replay keyed by everything the launch depends on
   uint64_t sigma_bits;
   memcpy(&sigma_bits, &sigma, 8);
-  std::array<uintptr_t, 13> key = {
+  std::array<uintptr_t, kGraphKeyLen> key = {
       (uintptr_t)mode | ((uintptr_t)c->S << 8), (uintptr_t)c->d_src_z,
       (uintptr_t)P, (uintptr_t)dtype, (uintptr_t)v, (uintptr_t)dobs,
       (uintptr_t)dseis, (uintptr_t)seis, (uintptr_t)misfit, (uintptr_t)grad,
       (uintptr_t)sigma_bits,
       ((uintptr_t)pl.Q << 32) | ((uintptr_t)pl.V << 16) | (uintptr_t)pl.T,
-      ((uintptr_t)pl.ncl << 32) | (uintptr_t)pl.K};
+      ((uintptr_t)pl.ncl << 32) | (uintptr_t)pl.K,
+      ((uintptr_t)pl.gw << 32) | (uintptr_t)pl.Hb,
+      ((uintptr_t)pl.spi << 32) | (uintptr_t)pl.ipp,
+      ((uintptr_t)pl.items << 32) | (uintptr_t)pl.nseg,
+      (uintptr_t)pl.smem};
   if (!c->use_graphs) {
-    if ((rc = prepare_wave(pl))) return rc;
+    if ((rc = prepare_wave(c, pl))) return rc;
     rc = enqueue_batched(c, pl, wp, P, sigma, misfit, st);
     c->last_stream = st;
     return rc;
@@ -554,7 +591,7 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
       return VIP_OK;
     }
   }
-  if ((rc = prepare_wave(pl))) return rc;
+  if ((rc = prepare_wave(c, pl))) return rc;
   cudaGraph_t graph;
   VIP_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   rc = enqueue_batched(c, pl, wp, P, sigma, misfit, c->cap_stream);
@@ -585,20 +622,28 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
   if (rc) return rc;
   std::sort(cand.begin(), cand.end(), [](const Plan &a, const Plan &b) { return a.est < b.est; });
   if (cand.size() > 6) cand.resize(6);
-  const int Nsave = c->N;
-  const int Ntune = std::min(c->N, 48);
-  float *tmp_out = nullptr;
-  double *tmp_mis = nullptr;
-  VIP_TRY(cudaMalloc(&tmp_mis, sizeof(double) * P));
   const size_t outn = mode == WM_FORWARD ? (size_t)P * c->S * c->R * c->N
                                          : (size_t)P * c->nz * c->nx;
-  VIP_TRY(cudaMalloc(&tmp_out, outn * 4));
-  cudaEvent_t e0, e1;
-  VIP_TRY(cudaEventCreate(&e0));
-  VIP_TRY(cudaEventCreate(&e1));
+  // every resource below is released on every return path
+  struct Held {
+    fwi_ctx *c;
+    int Nsave;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Held() {
+      c->N = Nsave;
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (out) cudaFree(out);
+    }
+  } h{c, c->N};
+  VIP_TRY(cudaMalloc(&h.out, outn * 4));
+  VIP_TRY(cudaEventCreate(&h.e0));
+  VIP_TRY(cudaEventCreate(&h.e1));
   float best = 1e30f;
-  std::array<int, 4> pick = {cand[0].Q, cand[0].V, cand[0].T, (int)cand[0].gw};
-  c->N = Ntune;
+  bool timed = false;
+  std::array<int, 4> pick = {0, 0, 0, 0};
+  c->N = std::min(c->N, 48);
   for (auto &pl0 : cand) {
     Plan pl = pl0;
     pl.K = 1;
@@ -607,35 +652,30 @@ static int autotune_plan(fwi_ctx *c, int P, int mode, int dtype, const float *v,
     plan_memory(c, pl, P);
     if (pl.total_bytes > free_budget(c)) continue;
     Tables *tb = nullptr;
-    if ((rc = get_tables(c, pl.Q, pl.V, &tb))) break;
-    if ((rc = ensure_scratch(c, pl.total_bytes))) break;
+    if ((rc = get_tables(c, pl.Q, pl.V, &tb))) return rc;
+    if ((rc = ensure_scratch(c, pl.total_bytes))) return rc;
     WaveParams wp;
-    if ((rc = fill_params(c, pl, tb, P, wp))) break;
+    if ((rc = fill_params(c, pl, tb, P, wp))) return rc;
     wp.P = P; wp.v = v; wp.dobs = dobs; wp.dseis = dseis;
-    wp.seis = tmp_out; wp.grad = tmp_out; wp.grad_atomic = 0;
+    wp.seis = h.out; wp.grad = h.out; wp.grad_atomic = 0;
     wp.rho_scale = 1.f;
     wp.items = pl.items;
-    if ((rc = prepare_wave(pl))) break;
-    for (int rep = 0; rep < 3 && rc == 0; ++rep) {
-      if (rep == 2) VIP_TRY(cudaEventRecord(e0, st));
-      rc = launch_wave(pl, wp, pl.ncl, st);
-      if (rep == 2) VIP_TRY(cudaEventRecord(e1, st));
+    if ((rc = prepare_wave(c, pl))) return rc;
+    for (int rep = 0; rep < 3; ++rep) {
+      if (rep == 2) VIP_TRY(cudaEventRecord(h.e0, st));
+      if ((rc = launch_wave(pl, wp, pl.ncl, st))) return rc;
+      if (rep == 2) VIP_TRY(cudaEventRecord(h.e1, st));
     }
-    if (rc) break;
-    VIP_TRY(cudaEventSynchronize(e1));
+    VIP_TRY(cudaEventSynchronize(h.e1));
     float ms = 0.f;
-    VIP_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    VIP_TRY(cudaEventElapsedTime(&ms, h.e0, h.e1));
     // normalise by the full problem's number of waves
     const float score = (float)(ms * idiv_up(pl0.items, pl0.ncl));
     if (score < best) { best = score; pick = {pl.Q, pl.V, pl.T, (int)pl.gw}; }
+    timed = true;
   }
-  c->N = Nsave;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(tmp_out);
-  cudaFree(tmp_mis);
-  if (rc) return rc;
-  c->tuned[std::make_tuple(P, mode * 16 + dtype, c->S)] = pick;
+  // nothing fitted the memory budget: leave the choice to the cost model
+  if (timed) c->tuned[std::make_tuple(P, mode * 16 + dtype, c->S)] = pick;
   (void)sigma;
   return VIP_OK;
 }
@@ -648,9 +688,11 @@ __global__ void plain_set_w(const float *v, int nz, int nx, int nb, int NZ, int 
   if (idx >= NZ * NX) return;
   const int z = idx / NX, x = idx - z * NX;
   const int iz = min(max(z - nb, 0), nz - 1), ix = min(max(x - nb, 0), nx - 1);
-  const float cc = __fmul_rn(v[(size_t)iz * nx + ix], dtdx);
+  const float vv = v[(size_t)iz * nx + ix];
+  const float cc = __fmul_rn(vv, dtdx);
   const float w = __fmul_rn(cc, cc);
   if (!(w <= wcfl)) atomicOr(status, 1);
+  if (!isfinite(vv)) atomicOr(status, 2);
   W[idx] = w;
 }
 
@@ -709,6 +751,7 @@ static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *d
   const size_t rhon = (size_t)c->R * N;
   const size_t need = align_up(Dn * 4, 256) + align_up(CKn * 4, 256) + align_up(ASn * 4, 256) +
                       align_up(rhon * 4, 256);
+  c->need_bytes = need;
   if (need > free_budget(c)) return VIP_ERR_NOMEM;
   if ((rc = ensure_scratch(c, need))) return rc;
   Carve cv(c->scratch, c->scratch_bytes);
@@ -806,7 +849,7 @@ static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *d
   }
   if (mode == WM_GRADIENT && misfit) {
     j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(c->pl_J, P, c->S, 1,
-                                                     0.5 / (sigma * sigma), misfit);
+                                                     0.5 / (sigma * sigma), misfit, c->d_status);
     VIP_CHECK_LAUNCH();
   }
   c->last_stream = st;
@@ -833,6 +876,7 @@ const char *vip_strerror(int code) {
     case VIP_ERR_TIMEOUT: return "bounded device wait expired";
     case VIP_ERR_NOTPD: return "kernel matrix not positive definite";
     case VIP_ERR_UNSUPPORTED: return "no feasible launch plan on this device";
+    case VIP_ERR_NONFINITE: return "non-finite input (NaN or infinity)";
   }
   return "unknown status";
 }
@@ -927,6 +971,7 @@ int fwi_set_mode(fwi_ctx *c, int mode, int ckpt_every) {
     return VIP_ERR_ARG;
   c->mode = mode;
   c->ckpt = ckpt_every;
+  vip::drop_graphs(c);
   return VIP_OK;
 }
 
@@ -936,12 +981,14 @@ int fwi_set_plan(fwi_ctx *c, int Q, int V, int T, int sources_per_item, int coef
     return VIP_ERR_ARG;
   c->force_Q = Q; c->force_V = V; c->force_T = T; c->force_spi = sources_per_item;
   c->force_coeff = coeff;
+  vip::drop_graphs(c);
   return VIP_OK;
 }
 
 int fwi_set_autotune(fwi_ctx *c, int enable) {
   if (!c) return VIP_ERR_ARG;
   c->autotune = enable ? 1 : 0;
+  vip::drop_graphs(c);
   return VIP_OK;
 }
 
@@ -956,6 +1003,7 @@ int fwi_query_plan(fwi_ctx *c, int P, int precision, int *plan_out, size_t *byte
   if (!c || P < 1 || !plan_out) return VIP_ERR_ARG;
   Plan pl;
   int rc = choose_plan(c, P, WM_GRADIENT, precision, pl);
+  if (rc == VIP_ERR_NOMEM && bytes_out) *bytes_out = c->need_bytes;
   if (rc) return rc;
   plan_out[0] = pl.Q; plan_out[1] = pl.V; plan_out[2] = pl.T; plan_out[3] = pl.Hb;
   plan_out[4] = pl.ncl; plan_out[5] = pl.K; plan_out[6] = pl.items; plan_out[7] = pl.spi;
@@ -1001,9 +1049,18 @@ int fwi_gradient_sources(fwi_ctx *c, const float *v, int P, const float *dobs, d
   if (c->mode == FWI_MODE_PLAIN) return VIP_ERR_UNSUPPORTED;
   const size_t trace = (size_t)c->R * c->N;
   if (!c->d_sub_z) {
-    VIP_TRY(cudaMalloc(&c->d_sub_z, sizeof(int) * c->S));
-    VIP_TRY(cudaMalloc(&c->d_sub_x, sizeof(int) * c->S));
-    VIP_TRY(cudaMalloc(&c->d_sub_dobs, sizeof(float) * trace * c->S));
+    // all three buffers or none: a partial allocation is released, so a later
+    // call retries instead of using a null table
+    int *sz_d = nullptr, *sx_d = nullptr;
+    float *do_d = nullptr;
+    if (cudaMalloc(&sz_d, sizeof(int) * c->S) != cudaSuccess ||
+        cudaMalloc(&sx_d, sizeof(int) * c->S) != cudaSuccess ||
+        cudaMalloc(&do_d, sizeof(float) * trace * c->S) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(sz_d); cudaFree(sx_d); cudaFree(do_d);
+      return VIP_ERR_NOMEM;
+    }
+    c->d_sub_z = sz_d; c->d_sub_x = sx_d; c->d_sub_dobs = do_d;
   }
   // gather the minibatch in front of the launch, in stream order (a copy from
   // pageable host memory returns once the source has been staged, so sz, sx
@@ -1038,12 +1095,15 @@ int fwi_adjoint(fwi_ctx *c, const float *v, int P, const float *dseis, float *gr
                      stream);
 }
 
+size_t fwi_bytes_needed(fwi_ctx *c) { return c ? c->need_bytes : 0; }
+
 int fwi_last_status(fwi_ctx *c) {
   if (!c) return VIP_ERR_ARG;
   if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) return VIP_ERR_CUDA;
   int h = 0;
   if (cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return VIP_ERR_CUDA;
+  if (h & 6) return VIP_ERR_NONFINITE;
   return (h & 1) ? VIP_ERR_CFL : VIP_OK;
 }
 

@@ -22,10 +22,12 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
 // c < d, with A [np][Kp] and B [dp][Kp] each given as three BF16 pieces
 // (h, m, l) multiplied with the six-product split (FP32-class accuracy).
 // np, dp multiples of 128, Kp of 64; q, lo, hi may be NULL. err as for
-// gram_tc_launch.
+// gram_tc_launch. skip (device word, may be NULL): when nonzero at the time
+// the kernel runs, X is left unchanged (an earlier kernel of the step saw a
+// non-finite input).
 int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const B[3], int n,
                      int d, int np, int dp, int Kp, const float *Xc, const float *rcoef,
                      const float *q, const float *lo, const float *hi, float *X, int *err,
-                     cudaStream_t st);
+                     const int *skip, cudaStream_t st);
 
 }  // namespace vip

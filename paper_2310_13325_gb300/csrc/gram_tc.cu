@@ -11,9 +11,12 @@
 //   - after the last block all four warps read the accumulator back with
 //     tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and store
 //     the partial tile.
-// Every mbarrier wait is bounded (about one second of clock cycles); on
-// expiry the kernel records bit 0 in *err, skips its remaining work, waits
-// for its outstanding copies with the same bound, frees TMEM and returns.
+// Every mbarrier wait is bounded (about one second of clock cycles by
+// default); on expiry the kernel records bit 0 in *err, skips its remaining
+// work, waits for the copies it has issued with the same bound, frees TMEM
+// and returns. A test hook (vip_test_set_wait) shortens the bound and can
+// stop the copy producer from issuing anything, so that the consumer's wait
+// expires on purpose without any fault.
 #include "gram.cuh"
 
 #include <cuda.h>
@@ -25,6 +28,11 @@ constexpr int GT_STAGES = 3;
 constexpr int GT_TILE_BYTES = 128 * 64 * 2;           // one operand tile
 constexpr int GT_STAGE_BYTES = 2 * GT_TILE_BYTES;     // A and B
 constexpr long long GT_WAIT_CYCLES = 2000000000ll;    // ~1 s at 2 GHz
+
+// Test hook state (host): the wait bound passed to the next launches and
+// whether their producers issue no copies.
+static long long g_wait_cycles = GT_WAIT_CYCLES;
+static int g_stall_producer = 0;
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -53,16 +61,27 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
 }
 
 // Bounded wait; returns false (and flags *err) when the bound expires.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err,
+                                          long long limit) {
   if (mbar_try(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(b, parity)) {
-    if (clock64() - t0 > GT_WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, 1);
       return false;
     }
   }
   return true;
+}
+
+// After an abort: wait (bounded) until every stage's last issued copy has
+// landed, so no bulk copy into this CTA's shared memory is left in flight.
+__device__ __forceinline__ void drain_issued(uint64_t *full_bar, int issued, int *err,
+                                             long long limit) {
+  for (int s = 0; s < GT_STAGES && s < issued; ++s) {
+    const int use = (issued - 1 - s) / GT_STAGES;   // last use of stage s issued
+    mbar_wait(&full_bar[s], (uint32_t)(use & 1), err, limit);
+  }
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -142,13 +161,14 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
                                                          const __grid_constant__ CUtensorMap mm,
                                                          const __grid_constant__ CUtensorMap ml,
                                                          int KB, int kper, int total, int np,
-                                                         float *parts, int *err) {
+                                                         float *parts, int *err,
+                                                         long long wait, int stall) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
   uint8_t *ring = (uint8_t *)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], done_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, n_issued;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int t = blockIdx.x, ti = 0;
@@ -173,6 +193,7 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
+    n_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -190,11 +211,11 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
 
   const int n_iter = g1 - g0;
   if (threadIdx.x == 0) {
-    // producer
-    for (int i = 0; i < n_iter; ++i) {
+    // producer (with the test hook's stall it issues nothing)
+    for (int i = 0; i < (stall ? 0 : n_iter); ++i) {
       const int s = i % GT_STAGES;
       const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err)) { abort_flag = 1; break; }
+      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err, wait)) { abort_flag = 1; break; }
       if (*(volatile int *)&abort_flag) break;
       const int g = g0 + i;
       const int pass = g / KB, kb = g - pass * KB;
@@ -206,14 +227,14 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
       mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
       tma_load_2d(sa, ma, &full_bar[s], kb * 64, ti * 128);
       tma_load_2d(sb, mb, &full_bar[s], kb * 64, tj * 128);
+      n_issued = i + 1;
     }
   } else if (threadIdx.x == 32) {
     // MMA issuer
-    bool ok = true;
     for (int i = 0; i < n_iter; ++i) {
       const int s = i % GT_STAGES;
       const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&full_bar[s], use & 1u, err)) { ok = false; abort_flag = 1; break; }
+      if (!mbar_wait(&full_bar[s], use & 1u, err, wait)) { abort_flag = 1; break; }
       tc_fence_after();
       const uint32_t sa = su32(ring + s * GT_STAGE_BYTES);
       const uint32_t sb = sa + GT_TILE_BYTES;
@@ -222,12 +243,11 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
         umma(tacc, sdesc(sa + k * 32), sdesc(sb + k * 32), (i > 0 || k > 0) ? 1u : 0u);
       umma_commit(&empty_bar[s]);
     }
-    (void)ok;
     umma_commit(&done_bar);
   }
   __syncwarp();
   // epilogue: wait for the accumulator
-  const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err));
+  const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err, wait));
   tc_fence_after();
   if (done && !*(volatile int *)&abort_flag) {
     const uint32_t lane_base = tacc + ((uint32_t)(warp * 32) << 16);
@@ -243,12 +263,7 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     }
   }
   // drain: every stage's copies must have landed before the CTA retires
-  if (threadIdx.x == 0 && abort_flag) {
-    for (int s = 0; s < GT_STAGES && s < n_iter; ++s) {
-      const int last = ((n_iter - 1 - s) / GT_STAGES);
-      mbar_wait(&full_bar[s], (uint32_t)(last & 1), err);
-    }
-  }
+  if (threadIdx.x == 0 && abort_flag) drain_issued(full_bar, n_issued, err, wait);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -273,12 +288,12 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
     const __grid_constant__ CUtensorMap bm, const __grid_constant__ CUtensorMap bl, int KB,
     int MT, int n, int d, const float *__restrict__ Xc, const float *__restrict__ rcoef,
     const float *__restrict__ q, const float *__restrict__ lo, const float *__restrict__ hi,
-    float *X, int *err) {
+    float *X, int *err, const int *skip, long long wait, int stall) {
   extern __shared__ __align__(1024) uint8_t usm_raw[];
   uint8_t *ring = (uint8_t *)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], done_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, n_issued;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ti = blockIdx.x % MT, tj = blockIdx.x / MT;
@@ -291,6 +306,7 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
+    n_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -308,10 +324,10 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
 
   const int n_iter = 6 * KB;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < n_iter; ++i) {
+    for (int i = 0; i < (stall ? 0 : n_iter); ++i) {
       const int s = i % GT_STAGES;
       const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err)) { abort_flag = 1; break; }
+      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err, wait)) { abort_flag = 1; break; }
       if (*(volatile int *)&abort_flag) break;
       const int pass = i / KB, kb = i - pass * KB;
       const int pa = kPassA[pass], pb = kPassB[pass];
@@ -322,12 +338,13 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
       mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
       tma_load_2d(sa, ma, &full_bar[s], kb * 64, ti * 128);
       tma_load_2d(sb, mb, &full_bar[s], kb * 64, tj * 128);
+      n_issued = i + 1;
     }
   } else if (threadIdx.x == 32) {
     for (int i = 0; i < n_iter; ++i) {
       const int s = i % GT_STAGES;
       const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&full_bar[s], use & 1u, err)) { abort_flag = 1; break; }
+      if (!mbar_wait(&full_bar[s], use & 1u, err, wait)) { abort_flag = 1; break; }
       tc_fence_after();
       const uint32_t sa = su32(ring + s * GT_STAGE_BYTES);
       const uint32_t sb = sa + GT_TILE_BYTES;
@@ -339,9 +356,11 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
     umma_commit(&done_bar);
   }
   __syncwarp();
-  const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err));
+  const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err, wait));
   tc_fence_after();
-  if (done && !*(volatile int *)&abort_flag) {
+  // a non-finite input reported by an earlier kernel of the step (*skip):
+  // the particles are left as they were
+  if (done && !*(volatile int *)&abort_flag && !(skip && *skip)) {
     const uint32_t lane_base = tacc + ((uint32_t)(warp * 32) << 16);
     const float rc = row < n ? rcoef[row] : 0.f;
     for (int ch = 0; ch < 4; ++ch) {
@@ -366,12 +385,7 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
       }
     }
   }
-  if (threadIdx.x == 0 && abort_flag) {
-    for (int s = 0; s < GT_STAGES && s < n_iter; ++s) {
-      const int last = ((n_iter - 1 - s) / GT_STAGES);
-      mbar_wait(&full_bar[s], (uint32_t)(last & 1), err);
-    }
-  }
+  if (threadIdx.x == 0 && abort_flag) drain_issued(full_bar, n_issued, err, wait);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -428,7 +442,7 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
                                (int)smem));
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   gram_tc_kernel<<<dim3(tiles, splits), 128, smem, st>>>(mh, mm, ml, KB, kper, total, np, parts,
-                                                         err);
+                                                         err, g_wait_cycles, g_stall_producer);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }
@@ -436,7 +450,7 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
 int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const Bm[3], int n,
                      int d, int np, int dp, int Kp, const float *Xc, const float *rcoef,
                      const float *q, const float *lo, const float *hi, float *X, int *err,
-                     cudaStream_t st) {
+                     const int *skip, cudaStream_t st) {
   if (np % 128 || dp % 128 || Kp % 64 || n > np || d > dp) return VIP_ERR_ARG;
   for (int k = 0; k < 3; ++k)
     if (((uintptr_t)A[k] & 15) || ((uintptr_t)Bm[k] & 15)) return VIP_ERR_ARG;
@@ -453,9 +467,17 @@ int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const
                                (int)smem));
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   update_tc_kernel<<<MT * NT, 128, smem, st>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], Kp / 64,
-                                               MT, n, d, Xc, rcoef, q, lo, hi, X, err);
+                                               MT, n, d, Xc, rcoef, q, lo, hi, X, err, skip,
+                                               g_wait_cycles, g_stall_producer);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }
 
 }  // namespace vip
+
+extern "C" int vip_test_set_wait(long long cycles, int stall_producer) {
+  if (cycles < 0 || stall_producer < 0 || stall_producer > 1) return VIP_ERR_ARG;
+  vip::g_wait_cycles = cycles == 0 ? vip::GT_WAIT_CYCLES : cycles;
+  vip::g_stall_producer = stall_producer;
+  return VIP_OK;
+}

@@ -69,6 +69,9 @@ static int gram_splits(int n, int d, int gp) {
 static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base, size_t cap,
                      SvgdWs &w) {
   Carve cv(base, cap);
+  // status words first (offset 0): [0] Cholesky failure, [1] Gram wait
+  // expired, [2] update wait expired, [3] non-finite input (bit 0 X, bit 1 G)
+  w.flag = cv.take<int>(4);
   w.np = (n + 127) / 128 * 128;
   w.dp = (d + 63) / 64 * 64;
   w.splits = gram_splits(n, d, gp);
@@ -86,7 +89,6 @@ static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base,
   w.hist = cv.take<unsigned int>(512);
   w.sel = cv.take<unsigned long long>(8);
   w.h2 = cv.take<double>(2);
-  w.flag = cv.take<int>(4);
   w.K = cv.take<float>((size_t)n * n);
   w.rs = cv.take<float>(n);
   w.Lk = cv.take<float>(stochastic ? (size_t)n * n : 0);
@@ -106,7 +108,7 @@ static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base,
 // ---------------------------------------------------------------------------
 __global__ void centre_kernel(const float *__restrict__ X, const float *__restrict__ q, int n,
                               int d, int dp, int np, double *mean, float *Xc, __nv_bfloat16 *Xh,
-                              __nv_bfloat16 *Xm, __nv_bfloat16 *Xl) {
+                              __nv_bfloat16 *Xm, __nv_bfloat16 *Xl, int *nonfinite) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= dp) return;
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
@@ -119,6 +121,7 @@ __global__ void centre_kernel(const float *__restrict__ X, const float *__restri
   }
   double s = 0.0;
   for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * d + c];
+  if (!isfinite(s)) atomicOr(nonfinite, 1);   // a NaN or infinity in the column
   const double m = s / n;
   mean[c] = m;
   const double sq = q ? sqrt((double)q[c]) : 1.0;   // Q-metric scale of the column
@@ -471,8 +474,9 @@ __global__ void split_b_kernel(const float *__restrict__ G, const float *__restr
                                const float *__restrict__ Xi, const double *h2p,
                                const float *__restrict__ q, int n, int d, int dp, int Kp,
                                float en, float gscale, float ns, __nv_bfloat16 *Bh,
-                               __nv_bfloat16 *Bm, __nv_bfloat16 *Bl) {
+                               __nv_bfloat16 *Bm, __nv_bfloat16 *Bl, int *nonfinite) {
   __shared__ float tile[32][33];
+  bool bad = false;
   const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   const float inv_h2 = (float)(1.0 / h2p[0]);
   for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
@@ -483,13 +487,16 @@ __global__ void split_b_kernel(const float *__restrict__ G, const float *__restr
       const float iq = q ? (float)(1.0 / qc) : 1.f, isq = q ? (float)(1.0 / sqrt(qc)) : 1.f;
       if (k < n) {
         const size_t g = (size_t)k * d + c;
-        v = en * (gscale * iq * G[g] - isq * inv_h2 * Xc[g]);
+        const float gv = G[g];
+        bad |= !isfinite(gv);
+        v = en * (gscale * iq * gv - isq * inv_h2 * Xc[g]);
       } else if (Xi && k < 2 * n) {
         v = ns * isq * Xi[(size_t)(k - n) * d + c];
       }
     }
     tile[kk][threadIdx.x] = v;
   }
+  if (bad) atomicOr(nonfinite, 2);
   __syncthreads();
   for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
     const int c = c0 + cc, k = k0 + threadIdx.x;
@@ -522,8 +529,9 @@ __global__ void __launch_bounds__(256) update_kernel(
     const float *__restrict__ K, const float *__restrict__ G, const float *__restrict__ Xc,
     const float *__restrict__ Lk, const float *__restrict__ Xi, const float *__restrict__ rs,
     const double *h2p, int n, int d, float eps, float gscale, float noise_scale,
-    const float *__restrict__ q, const float *lo, const float *hi, float *X) {
+    const float *__restrict__ q, const float *lo, const float *hi, float *X, int *nonfinite) {
   constexpr int BK = 16;
+  bool bad = false;
   __shared__ float Ks[BK][64], Ls[NOISE ? BK : 1][64];
   __shared__ __align__(16) float Gs[BK][64], Xs[BK][64], Es[NOISE ? BK : 1][64];
   const int c0 = blockIdx.x * 64, i0 = blockIdx.y * 64;
@@ -541,6 +549,7 @@ __global__ void __launch_bounds__(256) update_kernel(
       const bool ok = (j0 + kk < n) && (c0 + cc < d);
       const size_t g = (size_t)(j0 + kk) * d + c0 + cc;
       Gs[kk][cc] = ok ? G[g] : 0.f;
+      bad |= !isfinite(Gs[kk][cc]);
       Xs[kk][cc] = ok ? Xc[g] : 0.f;
       if (NOISE) Es[kk][cc] = ok ? Xi[g] : 0.f;
     }
@@ -567,6 +576,7 @@ __global__ void __launch_bounds__(256) update_kernel(
     }
     __syncthreads();
   }
+  if (bad) atomicOr(nonfinite, 2);
   const float inv_h2 = (float)(1.0 / h2p[0]);
   const float inv_n = 1.f / (float)n;
   for (int u = 0; u < 4; ++u) {
@@ -605,9 +615,10 @@ static int distances(const float *X, const float *q, int n, int d, float h2, int
                      double *h2_used, cudaStream_t st) {
   const bool tc = gp != VIP_GRAM_FP32;
   const bool x3 = gp == VIP_GRAM_BF16X3;
+  VIP_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), st));
   centre_kernel<<<idiv_up(w.dp, 128), 128, 0, st>>>(X, q, n, d, w.dp, w.np, w.mean, w.Xc,
                                                     tc ? w.Xh : nullptr, x3 ? w.Xm : nullptr,
-                                                    x3 ? w.Xl : nullptr);
+                                                    x3 ? w.Xl : nullptr, w.flag + 3);
   VIP_CHECK_LAUNCH();
   norms_kernel<<<n, 256, 0, st>>>(w.Xc, d, w.nrm);
   VIP_CHECK_LAUNCH();
@@ -671,12 +682,13 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
     split_a_kernel<<<1024, 256, 0, st>>>(w.K, Lk, n, w.unp, w.uKp, w.Ua[0], w.Ua[1], w.Ua[2]);
     VIP_CHECK_LAUNCH();
     split_b_kernel<<<dim3(w.udp / 32, w.uKp / 32), dim3(32, 8), 0, st>>>(
-        G, w.Xc, noise, w.h2, q, n, d, w.udp, w.uKp, en, gscale, ns, w.Ub[0], w.Ub[1], w.Ub[2]);
+        G, w.Xc, noise, w.h2, q, n, d, w.udp, w.uKp, en, gscale, ns, w.Ub[0], w.Ub[1], w.Ub[2],
+        w.flag + 3);
     VIP_CHECK_LAUNCH();
     rcoef_kernel<<<idiv_up(n, 256), 256, 0, st>>>(w.rs, w.h2, n, en, w.rcoef);
     VIP_CHECK_LAUNCH();
     int rc2 = update_tc_launch(w.Ua, w.Ub, n, d, w.unp, w.udp, w.uKp, w.Xc, w.rcoef, q, lo, hi,
-                               X, w.flag + 2, st);
+                               X, w.flag + 2, w.flag + 3, st);
     if (rc2) return rc2;
     poison_kernel<<<1024, 256, 0, st>>>(w.flag + 2, (size_t)n * d, X);
     VIP_CHECK_LAUNCH();
@@ -685,7 +697,7 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
   if (!stochastic && w.tcu) return tc_update(nullptr, nullptr, 0.f);
   if (!stochastic) {
     update_kernel<false><<<ug, 256, 0, st>>>(w.K, G, w.Xc, nullptr, nullptr, w.rs, w.h2, n, d,
-                                             eps, gscale, 0.f, q, lo, hi, X);
+                                             eps, gscale, 0.f, q, lo, hi, X, w.flag + 3);
     VIP_CHECK_LAUNCH();
     return VIP_OK;
   }
@@ -735,7 +747,7 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
     return VIP_OK;
   }
   update_kernel<true><<<ug, 256, 0, st>>>(w.K, G, w.Xc, w.Lk, noise, w.rs, w.h2, n, d, eps, gscale,
-                                          ns, q, lo, hi, X);
+                                          ns, q, lo, hi, X, w.flag + 3);
   VIP_CHECK_LAUNCH();
   // tau is a host local: make the asynchronous copy complete before return
   if (tau_used) VIP_TRY(cudaStreamSynchronize(st));
@@ -791,6 +803,16 @@ int svgd_step_noalloc(float *X, const float *G, float gscale, int n, int d, floa
   if (rc) return rc;
   return run_svgd(X, G, gscale, nullptr, n, d, eps, h2, lo, hi, gram_precision, ws,
                   kNoallocScratchBytes, h2_used, false, 0, 0, nullptr, nullptr, stream);
+}
+
+int svgd_status(const void *ws, vip_stream_t stream) {
+  if (!ws || ((uintptr_t)ws & 255)) return VIP_ERR_ARG;
+  int f[4] = {0, 0, 0, 0};
+  VIP_TRY(cudaMemcpyAsync(f, ws, sizeof f, cudaMemcpyDeviceToHost, stream));
+  VIP_TRY(cudaStreamSynchronize(stream));
+  if ((f[1] | f[2]) & 1) return VIP_ERR_TIMEOUT;
+  if (f[3]) return VIP_ERR_NONFINITE;
+  return VIP_OK;
 }
 
 size_t svgd_workspace_size(int n, int d, int gram_precision, int stochastic) {

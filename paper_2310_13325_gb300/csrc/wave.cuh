@@ -83,7 +83,8 @@ struct WaveParams {
   int grad_atomic;       // 1 when several work items share a particle: each
                          // item then writes its partial gradient to GI
   float *GI;             // [items][nz][nx] partial gradients (split items)
-  int *status;           // bit 0: CFL violation
+  int *status;           // bit 0: CFL violation; bit 1: non-finite velocity;
+                         // bit 2: non-finite misfit
   // per-cluster scratch slots
   void *Dbuf;   size_t Dslot;    // snapshot elements per slot
   float *Dscale; size_t DSslot;  // FP16 scales per slot
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
     const int s1 = min(p.S, s0 + p.spi);
     // model coefficients w' = (vpad dt/dx)^2 of this band; CFL check
     const float *vp = p.v + (size_t)pp * p.nz * p.nx;
-    bool cfl_bad = false;
+    bool cfl_bad = false, nonfinite = false;
     for (int q = tid; q < HW; q += T) {
       const int r = q / W4, x = q - r * W4;
       const int z = b * p.Hb + r;
@@ -763,9 +764,11 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
       if (z < p.NZ && x < p.NX) {
         const int iz = min(max(z - p.nb, 0), p.nz - 1);
         const int ix = min(max(x - p.nb, 0), p.nx - 1);
-        const float c = __fmul_rn(vp[(size_t)iz * p.nx + ix], p.dtdx);
+        const float vv = vp[(size_t)iz * p.nx + ix];
+        const float c = __fmul_rn(vv, p.dtdx);
         w = __fmul_rn(c, c);
         cfl_bad |= !(w <= p.w_cfl);
+        nonfinite |= !isfinite(vv);
       }
       if (GW) {
         p.Wg[(size_t)cid * p.Wgslot + (size_t)b * HW + q] = w;
@@ -776,6 +779,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
       }
     }
     if (cfl_bad) atomicOr(p.status, 1);
+    if (nonfinite) atomicOr(p.status, 2);
 
     for (int s = s0; s < s1; ++s) {
       const int pair = pp * p.S + s;

@@ -6,9 +6,9 @@ residuals. The misfit (Eq. 26) rounds each residual to FP32 once (2^-24), sums
 the squares of at most 64 residuals per thread in FP32 (4 receivers x 16
 steps: relative error <= 64 * 2^-24 ~ 3.8e-6) and accumulates those partial
 sums in FP64: the reduction is held to 4e-6 against an FP64 sum of the same
-GPU traces, and its value against the oracle to J_TOL, derived from the trace
-tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <= 2 (|d| / |r|) rel(d) with |d| / |r|
-<= 1.5 for prior particles, so 3e-5.
+GPU traces, and its value against the oracle to a tolerance derived per case
+from the trace tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <= 2 (|d| / |r|) rel(d) +
+4e-6, |d| / |r| measured on the oracle's traces (misfit_tolerance).
 Reduced-precision snapshots are measured and held to the bounds stated with
 each test.
 """
@@ -20,15 +20,20 @@ torch = pytest.importorskip("torch")
 import synth
 from oracle import fwi as ofwi
 import paper_2310_13325_gb300 as vg
-from gpu_common import cfg1_case, cfg1_oracle_gradients, odd_config, problem, rel
+from gpu_common import (cfg1_case, cfg1_oracle_gradients, misfit_tolerance, odd_config,
+                        oracle_gradients, problem, rel)
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-J_TOL = 3e-5
 
 
 def _t(a, dtype=torch.float32):
     return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def _cfg1_jtol(P=2):
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(P)
+    return misfit_tolerance(ofwi.seismograms(V, g), d_obs)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,7 +63,9 @@ def test_gradient_and_misfit_match_oracle_cfg1():
     G = G.reshape(2, -1).cpu().numpy()
     for p in range(2):
         assert rel(G[p], G_ref[p]) <= 1e-5, rel(G[p], G_ref[p])
-    assert np.all(np.abs(J - J_ref) <= J_TOL * np.abs(J_ref)), (J, J_ref)
+    jtol = _cfg1_jtol()
+    print("misfit rel. error %s, tolerance %.2e" % (np.abs(J - J_ref) / J_ref, jtol))
+    assert np.all(np.abs(J - J_ref) <= jtol * np.abs(J_ref)), (J, J_ref)
     # the reduction itself, on the GPU's own traces, against an FP64 sum
     tr = fwi.forward(_t(V)).double().cpu().numpy()
     J_host = 0.5 * ((tr - d_obs.astype(np.float32)[None]) ** 2).sum(axis=(1, 2, 3)) / sigma ** 2
@@ -108,20 +115,24 @@ def test_ragged_grid_every_launch_shape_agrees_with_oracle():
     cfg = odd_config()
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = problem(cfg, 3)
     J_ref, G_ref = ofwi.gradients(V, g, d_obs, sigma)
+    jtol = misfit_tolerance(ofwi.seismograms(V, g), d_obs)
     fwi = vg.Fwi.from_config(cfg, geo)
     Vt, Dt = _t(V), _t(d_obs)
     base = None
     # (Q, V, T, coefficients: 1 shared memory, 2 global memory)
     shapes = [(1, 4, 0, 1), (2, 4, 0, 1), (3, 8, 0, 1), (5, 4, 64, 1), (7, 4, 0, 1),
-              (2, 8, 96, 1), (1, 5, 0, 2), (3, 8, 0, 2), (4, 4, 64, 2), (2, 8, 96, 2)]
+              (2, 8, 96, 1), (1, 10, 0, 1), (2, 10, 96, 1), (4, 10, 0, 1),
+              (1, 5, 0, 2), (3, 8, 0, 2), (4, 4, 64, 2), (2, 8, 96, 2)]
     for Q, Vr, T, co in shapes:
         fwi.set_plan(Q, Vr, T, coeff=co)
-        assert fwi.query_plan(3)["coefficients"] == ("global" if co == 2 else "shared")
+        plan = fwi.query_plan(3)
+        assert plan["coefficients"] == ("global" if co == 2 else "shared")
+        assert (plan["cluster_ctas"], plan["rows_per_thread"]) == (Q, Vr), plan
         J, G = fwi.gradient(Vt, Dt, sigma)
         G = G.reshape(3, -1).cpu().numpy()
         for p in range(3):
             assert rel(G[p], G_ref[p]) <= 1e-5, (Q, Vr, T, co, p, rel(G[p], G_ref[p]))
-        assert np.all(np.abs(J.cpu().numpy() - J_ref) <= J_TOL * J_ref)
+        assert np.all(np.abs(J.cpu().numpy() - J_ref) <= jtol * J_ref)
         if base is None:
             base = G
         else:
@@ -158,32 +169,45 @@ def test_autograd_backward_is_the_oracle_adjoint():
         assert rel(got[p], ref[p]) <= 5e-5, rel(got[p], ref[p])
 
 
-# The imaging condition sums products mu^k D^k in which only the stored D^k is
-# rounded to the snapshot format, each by at most its unit roundoff u (2^-9 for
-# BF16, 2^-11 for FP16, whose per-block power-of-two scale keeps the values
-# normal), so the error is at most u times the sum of the terms' magnitudes.
-# The bound is u itself, which holds while the time sum does not cancel by more
-# than the margin; measured on the 64x64 case: 1.7e-4 (BF16), 2.1e-5 (FP16).
-@pytest.mark.parametrize("prec,bound", [(vg.FWI_CKPT_BF16, 2.0 ** -9),
-                                        (vg.FWI_CKPT_FP16, 2.0 ** -11)])
-def test_reduced_precision_snapshots_error_is_bounded(prec, bound):
+# The imaging condition sums products mu^k D^k in which only the stored
+# snapshot D^k is rounded, by at most the format's unit roundoff u (2^-8 for
+# BF16, 2^-11 for FP16), while mu and the FP32 forward sweep are unchanged. Per
+# cell, dJ/dv therefore moves by at most u times the sum of the magnitudes of
+# its imaging terms (M, from the oracle) plus the FP32 rounding of the two
+# accumulations over N steps (2 N 2^-24 M) and of the result (2 2^-24 M); FP16
+# values below the normal range after the per-block scaling carry an absolute
+# error under 2^-39 of the block's largest value (slack 1e-7 max M). Against
+# the oracle the gradient is stated, not gated: the time sum cancels, so the
+# relative L2 error is not bounded by u.
+@pytest.mark.parametrize("prec,u", [(vg.FWI_CKPT_BF16, 2.0 ** -8),
+                                    (vg.FWI_CKPT_FP16, 2.0 ** -11)])
+def test_reduced_precision_snapshots_error_is_bounded(prec, u):
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
-    J_ref, G_ref = cfg1_oracle_gradients(2)
+    J_ref, G_ref, M_ref, _ = oracle_gradients(g, V, range(g.nsrc), d_obs, sigma)
     fwi = vg.Fwi.from_config(cfg, geo)
+    J32, G32 = fwi.gradient(_t(V), _t(d_obs), sigma)
+    G32 = G32.reshape(2, -1).double().cpu().numpy()
     J, G = fwi.gradient(_t(V), _t(d_obs), sigma, precision=prec)
-    G = G.reshape(2, -1).cpu().numpy()
-    errs = [rel(G[p], G_ref[p]) for p in range(2)]
-    print("snapshot precision %d: gradient rel-L2 %s" % (prec, errs))
-    assert max(errs) <= bound
+    G = G.reshape(2, -1).double().cpu().numpy()
+    for p in range(2):
+        bound = (u + (2 * cfg.nt + 2) * 2.0 ** -24) * M_ref[p] * 1.001 + 1e-7 * M_ref[p].max()
+        print("snapshot precision %d, particle %d: gradient rel-L2 vs oracle %.2e; largest "
+              "|G - G_fp32| / bound %.3f" % (prec, p, rel(G[p], G_ref[p]),
+                                              (np.abs(G[p] - G32[p]) / bound).max()))
+        assert np.all(np.abs(G[p] - G32[p]) <= bound)
     # the misfit comes from the FP32 forward sweep and is unaffected
-    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= J_TOL * J_ref)
+    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= _cfg1_jtol() * J_ref)
     # the same snapshots with the coefficients in global memory: identical
-    fwi.set_plan(2, 4, 0, g.nsrc, coeff=2)
-    Jg, Gg = fwi.gradient(_t(V), _t(d_obs), sigma, precision=prec)
-    Jg, Gg = Jg.clone(), Gg.clone()
-    fwi.set_plan(2, 4, 0, g.nsrc, coeff=1)
-    Js, Gs = fwi.gradient(_t(V), _t(d_obs), sigma, precision=prec)
-    assert torch.equal(Gg, Gs) and torch.equal(Jg, Js)
+    # (a fresh context per layout, so no cached launch is shared between them)
+    out = {}
+    for co in (1, 2):
+        f = vg.Fwi.from_config(cfg, geo)
+        f.set_plan(2, 4, 0, g.nsrc, coeff=co)
+        assert f.query_plan(2, prec)["coefficients"] == ("global" if co == 2 else "shared")
+        Jc, Gc = f.gradient(_t(V), _t(d_obs), sigma, precision=prec)
+        out[co] = (Jc.clone(), Gc.clone())
+        f.close()
+    assert torch.equal(out[1][1], out[2][1]) and torch.equal(out[1][0], out[2][0])
 
 
 @pytest.mark.parametrize("K", [1, 9])
@@ -193,12 +217,14 @@ def test_global_coefficients_equal_shared_bit_for_bit(K):
     shared-memory layout, with and without restart checkpoints, and the
     adjoint-only mode agrees too."""
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
-    fwi = vg.Fwi.from_config(cfg, geo)
     Vt, Dt = _t(V), _t(d_obs)
-    fwi.set_mode(vg.FWI_MODE_BATCHED, K)
     out = {}
     for co in (1, 2):
+        # a fresh context per layout: no cached launch is shared between them
+        fwi = vg.Fwi.from_config(cfg, geo)
+        fwi.set_mode(vg.FWI_MODE_BATCHED, K)
         fwi.set_plan(3, 8, 0, g.nsrc, coeff=co)
+        assert fwi.query_plan(2)["coefficients"] == ("global" if co == 2 else "shared")
         S = fwi.forward(Vt).clone()
         J, G = fwi.gradient(Vt, Dt, sigma)
         J, G = J.clone(), G.clone()
@@ -236,7 +262,7 @@ def test_single_particle_and_source_split_work_items():
     plan = fwi.query_plan(1)
     J, G = fwi.gradient(_t(V[:1]), _t(d_obs), sigma)
     assert rel(G.reshape(-1).cpu().numpy(), G_ref[0]) <= 1e-5
-    assert abs(J.item() - J_ref[0]) <= J_TOL * J_ref[0]
+    assert abs(J.item() - J_ref[0]) <= _cfg1_jtol() * J_ref[0]
     assert plan["sources_per_item"] >= 1
 
 
@@ -326,7 +352,8 @@ def test_source_minibatch_gradient_matches_oracle():
     Gh = Ga.reshape(2, -1).cpu().numpy()
     for p in range(2):
         assert rel(Gh[p], G_ref[p]) <= 1e-5, rel(Gh[p], G_ref[p])
-    assert np.all(np.abs(Ja.cpu().numpy() - J_ref) <= J_TOL * J_ref)
+    sub = np.stack([ofwi.seismograms(V, g)[:, s] for s in (3, 1)], axis=1)
+    assert np.all(np.abs(Ja.cpu().numpy() - J_ref) <= misfit_tolerance(sub, d_obs[[3, 1]]) * J_ref)
     Jb, Gb = fwi.gradient(Vt, Dt, sigma, sources=[0, 2])
     Gs = (Ga + Gb).reshape(2, -1).cpu().numpy()
     Gf = G0.reshape(2, -1).cpu().numpy()
