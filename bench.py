@@ -14,9 +14,12 @@ during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank runs an independent replica of the
-workload (different particle seed); value sums the ranks' particles over the
-slowest rank's time.
+Under torchrun (N > 1) the particles are split across the ranks: every rank
+holds 600 particles (its own seed) and computes their gradients alone; the
+SVGD update couples the whole ensemble of 600 N particles, so each iteration
+all-gathers the particles and gradients (NCCL) and every rank applies the
+update to the whole ensemble (paper_2310_13325_gb300.sharded). value sums the
+ranks' particles over the slowest rank's time.
 """
 import argparse
 import json
@@ -84,6 +87,9 @@ def parse():
                     help="coordinates per particle of the update workload")
     ap.add_argument("--stochastic", action="store_true",
                     help="update workload: ssvgd_step with injected noise")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="collective backend of multi-rank runs (gloo: several ranks "
+                         "sharing one GPU, gathering through host memory)")
     return ap.parse_args()
 
 
@@ -179,6 +185,7 @@ def build_problem(cfg, P, rank, dev, vg, torch):
 def run_ours(args, cfg, P, torch, ws_, rank, local):
     import paper_2310_13325_gb300 as vg
     from paper_2310_13325_gb300 import build as vbuild
+    from paper_2310_13325_gb300 import sharded
     vbuild.build()
     dev = torch.device("cuda:%d" % local)
     torch.cuda.set_device(dev)
@@ -195,7 +202,8 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     hi_t = torch.tensor(hi.reshape(-1), dtype=torch.float32, device=dev)
     misfit = torch.empty(P, dtype=torch.float64, device=dev)
     grad = torch.empty((P, cfg.nz, cfg.nx), dtype=torch.float32, device=dev)
-    ws = torch.empty(vg.svgd_workspace_size(P, cfg.d, gram, False), dtype=torch.uint8,
+    # the update sees the whole ensemble: P particles on each of the ws_ ranks
+    ws = torch.empty(vg.svgd_workspace_size(P * ws_, cfg.d, gram, False), dtype=torch.uint8,
                      device=dev)
     h2 = torch.empty(1, dtype=torch.float64, device=dev)
     qv = torch.empty(cfg.d, dtype=torch.float32, device=dev)
@@ -208,8 +216,13 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
         fwi.gradient(X, dobs, sigma, precision=prec, misfit=misfit, grad=grad)
         if "eps" not in eps_box:
             # step size: the first update moves the fastest coordinate ~20 m/s
-            g = grad.abs().max().item()
-            eps_box["eps"] = 20.0 / max(g, 1e-30)
+            # (of the whole ensemble: every rank must apply the same update)
+            g = grad.abs().max().reshape(1).double()
+            if ws_ > 1:
+                if args.dist_backend == "gloo":
+                    g = g.cpu()
+                torch.distributed.all_reduce(g, op=torch.distributed.ReduceOp.MAX)
+            eps_box["eps"] = 20.0 / max(g.item(), 1e-30)
         svgd_update()
 
     uncon = args.svgd_space == "unconstrained"
@@ -221,7 +234,27 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     theta = vg.to_unconstrained(X, lo_t, hi_t) if uncon else None
     gth = torch.empty_like(X) if uncon else None
 
+    def update_model_space(Xf, Gf):
+        q = vg.svgd_inverse_variance(Xf) if diag else None
+        vg.svgd_step(Xf, Gf, eps_box["eps"], lo=lo_t, hi=hi_t, gram_precision=gram, ws=ws,
+                     h2_used=h2, gscale=-1.0, q=q)
+
+    def update_unconstrained(Xf, Gf):
+        th = vg.to_unconstrained(Xf, lo_t, hi_t)
+        gt = vg.unconstrained_gradient(th, Gf, lo_t, hi_t, gscale=-1.0)
+        if "eps_t" not in eps_box:
+            eps_box["eps_t"] = 0.1 / max(gt.abs().max().item(), 1e-30)
+        q = vg.svgd_inverse_variance(th) if diag else None
+        vg.svgd_step(th, gt, eps_box["eps_t"], gram_precision=gram, ws=ws, h2_used=h2, q=q)
+        vg.to_model(th, lo_t, hi_t, out=Xf)
+
     def svgd_update():
+        if ws_ > 1:
+            # particles split across ranks: one all-gather, the update of the
+            # whole ensemble on every rank, each keeps its rows
+            sharded.sharded_update(X, grad.reshape(P, -1),
+                                   update_unconstrained if uncon else update_model_space)
+            return
         if not uncon:
             q = vg.svgd_inverse_variance(X, out=qv) if diag else None
             vg.svgd_step(X, grad.reshape(P, -1), eps_box["eps"], lo=lo_t, hi=hi_t,
@@ -833,8 +866,7 @@ def run_update(args, torch):
 
 
 def reduce_over_ranks(t_ms, e2e_ms, device):
-    """Slowest rank's step time and end-to-end time (max over ranks). Every
-    rank runs an independent replica; no data crosses ranks."""
+    """Slowest rank's step time and end-to-end time (max over ranks)."""
     import torch
     t = torch.tensor([t_ms, e2e_ms or 0.0], dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -869,12 +901,13 @@ def main():
         return
     if ws_ > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        torch.distributed.init_process_group(args.dist_backend)
     res = run_ours(args, cfg, P, torch, ws_, rank, local)
     t_max = res["t_step_ms"]
     e2e_max = res.get("e2e_ms")
     if ws_ > 1:
-        t_max, e2e_max = reduce_over_ranks(t_max, e2e_max, "cuda:%d" % local)
+        t_max, e2e_max = reduce_over_ranks(t_max, e2e_max, "cpu" if args.dist_backend == "gloo"
+                                           else "cuda:%d" % local)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
