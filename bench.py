@@ -187,7 +187,10 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     from paper_2310_13325_gb300 import build as vbuild
     from paper_2310_13325_gb300 import sharded
     vbuild.build()
-    dev = torch.device("cuda:%d" % local)
+    # one GPU per rank; ranks beyond the visible GPUs (gloo runs that share a
+    # GPU) wrap around
+    gpu = local % max(1, torch.cuda.device_count())
+    dev = torch.device("cuda:%d" % gpu)
     torch.cuda.set_device(dev)
     prec = {"fp32": vg.FWI_FP32, "bf16": vg.FWI_CKPT_BF16, "fp16": vg.FWI_CKPT_FP16}[args.precision]
     gram = vg.VIP_GRAM_BF16X3 if args.precision == "fp32" else vg.VIP_GRAM_BF16
@@ -277,7 +280,7 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(gpu)
     if ws_ > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -907,7 +910,7 @@ def main():
     e2e_max = res.get("e2e_ms")
     if ws_ > 1:
         t_max, e2e_max = reduce_over_ranks(t_max, e2e_max, "cpu" if args.dist_backend == "gloo"
-                                           else "cuda:%d" % local)
+                                           else "cuda:%d" % (local % torch.cuda.device_count()))
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
