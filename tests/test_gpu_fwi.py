@@ -141,9 +141,11 @@ def test_ragged_grid_every_launch_shape_agrees_with_oracle():
 
 def test_autograd_backward_is_the_oracle_adjoint():
     """FwiSeis backward (fwi_adjoint) for the misfit's own upstream
-    sensitivity equals fwi_gradient and the oracle; for a white-noise upstream
-    sensitivity the FP32 arithmetic floor is higher (an FP32 emulation of the
-    recurrence in numpy gives 2.4e-5 for one source), so 5e-5 holds there."""
+    sensitivity equals fwi_gradient and the oracle to 1e-5. For a white-noise
+    upstream sensitivity the imaging time sum cancels far more: with every
+    term mu^k D^k held to a relative 1e-5 (the FP32 field bound), the gradient
+    moves by at most 1e-5 of the sum of the terms' magnitudes M, i.e. a
+    relative error of 1e-5 kappa with kappa = |M| / |G| from the oracle."""
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
     J_ref, G_ref = cfg1_oracle_gradients(2)
     fwi = vg.Fwi.from_config(cfg, geo)
@@ -159,14 +161,27 @@ def test_autograd_backward_is_the_oracle_adjoint():
         assert rel(got[p], G[p]) <= 1e-6, rel(got[p], G[p])
     rng = np.random.default_rng(12)
     dseis = rng.standard_normal((2, g.nsrc, g.nrec, g.nt))
-    ref = np.stack([ofwi.adjoint_of_upstream(V[p], g, dseis[p]).reshape(-1)
-                    for p in range(2)])
+    ref, mag = [], []
+    for p in range(2):
+        gp_ = np.zeros((cfg.nz, cfg.nx))
+        mp_ = np.zeros((cfg.nz, cfg.nx))
+        for s in range(g.nsrc):
+            _, gs, ms = ofwi.pair_gradient(V[p].reshape(cfg.nz, cfg.nx), g, s,
+                                           lambda tr, s=s, p=p: dseis[p, s], magnitude=True)
+            gp_ += gs
+            mp_ += ms
+        ref.append(gp_.reshape(-1))
+        mag.append(mp_.reshape(-1))
     v.grad = None
     seis = vg.FwiSeis.apply(v, fwi)
     (seis * _t(dseis)).sum().backward()
     got = v.grad.reshape(2, -1).cpu().numpy()
     for p in range(2):
-        assert rel(got[p], ref[p]) <= 5e-5, rel(got[p], ref[p])
+        kappa = np.linalg.norm(mag[p]) / np.linalg.norm(ref[p])
+        e = rel(got[p], ref[p])
+        print("white-noise upstream, particle %d: rel-L2 %.2e, kappa %.1f, tolerance %.2e"
+              % (p, e, kappa, 1e-5 * kappa))
+        assert e <= 1e-5 * kappa, (p, e, kappa)
 
 
 # The imaging condition sums products mu^k D^k in which only the stored
