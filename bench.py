@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fill", action="store_true",
+                    help="no second launch on the SMs the batched launch leaves idle")
     ap.add_argument("--plan", default="",
                     help="force the wave launch shape Q,V,T,coeff (cluster CTAs, rows per "
                          "thread, threads, 1 = coefficients in shared / 2 = in global "
@@ -196,6 +198,7 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     gram = vg.VIP_GRAM_BF16X3 if args.precision == "fp32" else vg.VIP_GRAM_BF16
     geo, fwi, X0, dobs_h, sigma, lo, hi = build_problem(cfg, P, rank, dev, vg, torch)
     fwi.set_autotune(not args.no_autotune)
+    fwi.set_fill(not args.no_fill)
     if args.plan:
         q, v, t, coeff = (int(x) for x in args.plan.split(","))
         fwi.set_plan(q, v, t, 0, coeff=coeff)
@@ -306,8 +309,10 @@ def run_ours(args, cfg, P, torch, ws_, rank, local):
     t_svgd = float(np.mean(svgd_ms))
     assert torch.isfinite(X).all().item() and torch.isfinite(misfit).all().item()
 
+    plan = fwi.query_plan(P, prec)
+    plan["fill"] = fwi.query_fill(P, prec)
     out = {"t_step_ms": t_step, "t_fwi_ms": t_fwi, "t_svgd_ms": t_svgd, "clocks": clocks,
-           "plan": fwi.query_plan(P, prec), "misfit_mean": float(misfit.mean().item()),
+           "plan": plan, "misfit_mean": float(misfit.mean().item()),
            "eps": eps_box["eps"], "h2": float(h2.item())}
 
     # end to end through the public API with host buffers: pinned inputs in,
@@ -374,9 +379,11 @@ SVGD_STEP_LAUNCHES = 28
 
 
 def fwi_gradient_launches(plan, nsrc):
-    """The persistent wave kernel, the per-item gradient merge when several work
-    items share a particle, and the misfit reduction."""
-    return 1 + (nsrc // plan["sources_per_item"] > 1) + 1
+    """The persistent wave kernel (and its fill launch on the idle SMs, when
+    there is one), the per-item gradient merge when several work items share a
+    particle, and the misfit reduction."""
+    fill = 1 if (plan.get("fill") or {}).get("clusters") else 0
+    return 1 + fill + (nsrc // plan["sources_per_item"] > 1) + 1
 
 
 # FP32 lane operations (FADD, FMUL, FFMA: one per lane, packed f32x2 counted

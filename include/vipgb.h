@@ -143,6 +143,21 @@ int  fwi_autotune(fwi_ctx *ctx, int P, int precision);
 int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T, int sources_per_item, int coeff);
 int  fwi_set_autotune(fwi_ctx *ctx, int enable);
 
+/* Fill launch. Clusters of the batched launch's shape cannot be placed on
+ * every SM (on the GB300, 36 clusters of 4 CTAs take 144 of the 152 SMs).
+ * With filling enabled (the default) and an automatically chosen plan with
+ * more work items than clusters, a second launch of smaller clusters (the
+ * global-coefficient layout, whose taller band fits shared memory) runs on
+ * the SMs left idle, at a lower priority, and both launches draw the work
+ * items from one counter. Results do not depend on which launch computed an
+ * item (every cell update, accumulation and per-receiver misfit sum is
+ * evaluated identically). fwi_set_fill(ctx, 0) disables it; forced plans
+ * (fwi_set_plan) never fill. fwi_query_fill writes 4 ints to fill_out
+ * (host): {cluster_ctas, rows_per_thread, threads, clusters} of the fill
+ * launch a gradient call for P particles would add, or zeros. */
+int  fwi_set_fill(fwi_ctx *ctx, int enable);
+int  fwi_query_fill(fwi_ctx *ctx, int P, int precision, int *fill_out);
+
 /* Describe the plan chosen for P particles: writes 10 ints to plan_out
  * (host): {cluster_ctas, rows_per_thread, threads, band_rows, concurrent
  * pairs, ckpt_every, work_items, sources_per_item, coeff (1 shared, 2

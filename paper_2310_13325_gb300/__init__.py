@@ -114,6 +114,18 @@ class Fwi:
     def set_autotune(self, enable=True):
         check(self._L.fwi_set_autotune(self._h, int(bool(enable))), "fwi_set_autotune")
 
+    def set_fill(self, enable=True):
+        """Enable or disable the second launch on the SMs the batched launch
+        leaves idle (fwi_set_fill)."""
+        check(self._L.fwi_set_fill(self._h, int(bool(enable))), "fwi_set_fill")
+
+    def query_fill(self, P, precision=FWI_FP32):
+        """Shape of the fill launch a gradient call for P particles would add
+        (all zeros: none)."""
+        out = (ctypes.c_int * 4)()
+        check(self._L.fwi_query_fill(self._h, int(P), int(precision), out), "fwi_query_fill")
+        return dict(zip(("cluster_ctas", "rows_per_thread", "threads", "clusters"), list(out)))
+
     def query_plan(self, P, precision=FWI_FP32):
         out = (ctypes.c_int * 10)()
         nb = ctypes.c_size_t()

@@ -43,6 +43,8 @@ _SIGS = {
                             c_void_p]),
     "fwi_last_status": (c_int, [c_void_p]),
     "fwi_bytes_needed": (c_size_t, [c_void_p]),
+    "fwi_set_fill": (c_int, [c_void_p, c_int]),
+    "fwi_query_fill": (c_int, [c_void_p, c_int, c_int, c_int_p]),
     "svgd_status": (c_int, [c_void_p, c_void_p]),
     "vip_test_set_wait": (c_int, [ctypes.c_longlong, c_int]),
     "svgd_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int]),

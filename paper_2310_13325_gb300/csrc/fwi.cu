@@ -56,7 +56,7 @@ struct Tables {
   int rmax = 0;   // largest number of receivers in one band
 };
 
-constexpr int kGraphKeyLen = 17;
+constexpr int kGraphKeyLen = 18;
 struct GraphEntry {
   std::array<uintptr_t, kGraphKeyLen> key;
   cudaGraphExec_t exec;
@@ -87,6 +87,10 @@ struct fwi_ctx {
   int force_Q = 0, force_V = 0, force_T = 0, force_spi = 0;          // launch override
   int force_coeff = 0;   // 0 any, 1 coefficients in shared memory, 2 in global memory
   int use_graphs = 1;   // VIPGB_GRAPHS=0 in the environment: eager launches
+  int fill = 1;         // second launch on the SMs the main launch leaves idle
+  cudaStream_t fill_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int prio_hi = 0, prio_lo = 0;
   size_t need_bytes = 0;   // device bytes the last planned call needs (or lacked)
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
@@ -231,7 +235,7 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
                   a(pl.Ggslot, 4);
   const size_t gi = (pl.mode != WM_FORWARD && pl.ipp > 1)
                         ? align_up((size_t)P * pl.ipp * c->nz * c->nx * 4, 256) : 0;
-  pl.total_bytes = align_up((size_t)P * c->S * pl.Q * 8, 256) + gi +
+  pl.total_bytes = 256 + align_up((size_t)P * c->S * c->R * 8, 256) + gi +
                    (size_t)pl.ncl * pl.slot_bytes;
 }
 
@@ -406,6 +410,42 @@ static void drop_graphs(fwi_ctx *c) {
   c->graphs.clear();
 }
 
+// A second launch for the SMs the main launch leaves idle (clusters of the
+// main shape cannot be placed on every SM: on the GB300 36 four-CTA clusters
+// take 144 of its 152 SMs). Its clusters are smaller, use the
+// global-coefficient layout so that their taller band fits shared memory, and
+// draw work items from the counter the main launch uses. Only for automatic
+// plans, when the main launch has more items than clusters; the plan that
+// puts the most idle SMs to work wins, then the cheaper one.
+static bool choose_fill(fwi_ctx *c, const Plan &mn, int P, Plan &fp) {
+  if (!c->fill || c->force_Q || c->force_V || c->force_T || c->force_coeff || c->force_spi)
+    return false;
+  if (mn.items <= mn.ncl) return false;
+  const int idle = c->sm_count - mn.Q * mn.ncl;
+  if (idle < 2) return false;
+  std::vector<Plan> cand;
+  c->force_coeff = 2;
+  const int rc = make_candidates(c, P, mn.mode, mn.dtype, cand);
+  c->force_coeff = 0;
+  if (rc) {
+    cudaGetLastError();
+    return false;
+  }
+  const Plan *best = nullptr;
+  auto used = [&](const Plan &q) { return std::min(q.maxcl, idle / q.Q) * q.Q; };
+  for (auto &q : cand) {
+    if (q.Q >= mn.Q || used(q) < 2) continue;
+    if (!best || used(q) > used(*best) || (used(q) == used(*best) && q.est < best->est))
+      best = &q;
+  }
+  if (!best) return false;
+  fp = *best;
+  fp.ipp = mn.ipp; fp.spi = mn.spi; fp.items = mn.items; fp.K = mn.K;
+  fp.ncl = used(fp) / fp.Q;
+  plan_memory(c, fp, P);
+  return true;
+}
+
 static int ensure_scratch(fwi_ctx *c, size_t bytes) {
   if (bytes <= c->scratch_bytes) return VIP_OK;
   drop_graphs(c);
@@ -434,19 +474,48 @@ __global__ void grad_merge_kernel(const float *GI, int P, int ipp, int d, float 
   grad[q] = acc;
 }
 
-__global__ void j_reduce_kernel(const double *Jpart, int P, int S, int Q, double scale,
-                                double *misfit, int *status) {
+// Misfit of each particle from its per-receiver sums Jrec [P][S*R] (FP64): one
+// block per particle, a fixed strided split over the threads and a fixed
+// reduction tree, so the result does not depend on how the wave kernel split
+// the grid or the work.
+constexpr int kJThreads = 256;
+__global__ void __launch_bounds__(kJThreads) j_reduce_kernel(const double *Jrec, int SR,
+                                                             double scale, double *misfit,
+                                                             int *status) {
+  __shared__ double red[kJThreads];
+  const int p = blockIdx.x;
+  double t = 0.0;
+  for (int k = threadIdx.x; k < SR; k += kJThreads) t += Jrec[(size_t)p * SR + k];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = kJThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    misfit[p] = red[0] * scale;
+    // a non-finite misfit (non-finite observed data or wavefield) is reported
+    if (!isfinite(red[0])) atomicOr(status, 4);
+  }
+}
+
+// Misfit of the plain path: one accumulator per (particle, source).
+__global__ void j_pairs_kernel(const double *Jpair, int P, int S, double scale, double *misfit,
+                               int *status) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double t = 0.0;
-  for (int s = 0; s < S; ++s)
-    for (int b = 0; b < Q; ++b) t += Jpart[((size_t)p * S + s) * Q + b];
+  for (int s = 0; s < S; ++s) t += Jpair[(size_t)p * S + s];
   misfit[p] = t * scale;
-  // a non-finite misfit (non-finite observed data or wavefield) is reported
   if (!isfinite(t)) atomicOr(status, 4);
 }
 
-static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams &wp) {
+// Kernel parameters of one launch. Scratch layout: the work counter, the
+// per-receiver misfit sums, the per-item gradients, the main launch's slots,
+// then (fill launch) its own slots. main_of_fill: the main plan when pl is the
+// fill launch's; use_work: draw items from the shared counter.
+static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams &wp,
+                       const Plan *main_of_fill = nullptr, bool use_work = false) {
   memset(&wp, 0, sizeof wp);
   wp.nz = c->nz; wp.nx = c->nx; wp.nb = c->nb; wp.NZ = c->NZ; wp.NX = c->NX;
   wp.N = c->N; wp.S = c->S; wp.R = c->R;
@@ -466,10 +535,14 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   wp.grad_atomic = pl.ipp > 1;
   // scratch carve
   Carve cv(c->scratch, c->scratch_bytes);
-  wp.Jpart = cv.take<double>((size_t)P * c->S * pl.Q);
+  int *work = cv.take<int>(64);
+  wp.work = use_work ? work : nullptr;
+  wp.Jrec = cv.take<double>((size_t)P * c->S * c->R);
   wp.GI = cv.take<float>((pl.mode != WM_FORWARD && pl.ipp > 1)
                              ? (size_t)P * pl.ipp * c->nz * c->nx : 0);
-  char *slots = cv.take<char>((size_t)pl.ncl * pl.slot_bytes);
+  const Plan &first = main_of_fill ? *main_of_fill : pl;
+  char *slots = cv.take<char>((size_t)first.ncl * first.slot_bytes);
+  if (main_of_fill) slots = cv.take<char>((size_t)pl.ncl * pl.slot_bytes);
   size_t off = 0;
   auto sub = [&](size_t n, size_t es) {
     char *r = slots + off;
@@ -499,7 +572,10 @@ static int prepare_wave(fwi_ctx *c, const Plan &pl) {
   return set_wave_attrs(c, fn);
 }
 
-static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream_t st) {
+// One launch of the wave kernel; prio (a stream-priority value, 0 = the
+// default) orders the placement of its clusters against a concurrent launch.
+static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream_t st,
+                       int prio = 0) {
   const void *fn = kernel_ptr(pl.V, pl.mode, pl.dtype, pl.gw);
   if (!fn) return VIP_ERR_UNSUPPORTED;
   cudaLaunchConfig_t cfg = {};
@@ -507,10 +583,12 @@ static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream
   cfg.blockDim = dim3(pl.T, 1, 1);
   cfg.dynamicSmemBytes = pl.smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = pl.Q; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
-  cfg.attrs = at; cfg.numAttrs = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = prio;
+  cfg.attrs = at; cfg.numAttrs = prio ? 2 : 1;
   WaveParams local = wp;
   void *args[1] = {&local};
   VIP_TRY(cudaLaunchKernelExC(&cfg, fn, args));
@@ -520,10 +598,24 @@ static int launch_wave(const Plan &pl, const WaveParams &wp, int ncl, cudaStream
 // Enqueue one batched call (no graph): status reset, optional grad zeroing,
 // the persistent kernel, the misfit reduction.
 static int enqueue_batched(fwi_ctx *c, const Plan &pl, WaveParams &wp, int P, double sigma,
-                           double *misfit, cudaStream_t st) {
+                           double *misfit, cudaStream_t st, const Plan *fp = nullptr,
+                           const WaveParams *wpf = nullptr) {
   VIP_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
-  int rc = launch_wave(pl, wp, pl.ncl, st);
-  if (rc) return rc;
+  int rc;
+  if (fp) {
+    // the fill launch runs on its own stream, joined before the reductions;
+    // the main launch has the higher priority, so its clusters are placed
+    // first and the fill's take the SMs left over
+    VIP_TRY(cudaMemsetAsync(wp.work, 0, sizeof(int), st));
+    VIP_TRY(cudaEventRecord(c->ev_fork, st));
+    VIP_TRY(cudaStreamWaitEvent(c->fill_stream, c->ev_fork, 0));
+    if ((rc = launch_wave(pl, wp, pl.ncl, st, c->prio_hi))) return rc;
+    if ((rc = launch_wave(*fp, *wpf, fp->ncl, c->fill_stream, c->prio_lo))) return rc;
+    VIP_TRY(cudaEventRecord(c->ev_join, c->fill_stream));
+    VIP_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
+  } else if ((rc = launch_wave(pl, wp, pl.ncl, st))) {
+    return rc;
+  }
   if (pl.mode != WM_FORWARD && wp.grad_atomic) {
     const size_t tot = (size_t)P * c->nz * c->nx;
     grad_merge_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(wp.GI, P, pl.ipp,
@@ -532,8 +624,7 @@ static int enqueue_batched(fwi_ctx *c, const Plan &pl, WaveParams &wp, int P, do
   }
   if (pl.mode == WM_GRADIENT && misfit) {
     const double scale = 0.5 / (sigma * sigma);
-    j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(wp.Jpart, P, c->S, pl.Q, scale, misfit,
-                                                     c->d_status);
+    j_reduce_kernel<<<P, kJThreads, 0, st>>>(wp.Jrec, c->S * c->R, scale, misfit, c->d_status);
     VIP_CHECK_LAUNCH();
   }
   return VIP_OK;
@@ -551,19 +642,30 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
     if (rc) return rc;
     if (!c->tuned.count(tkey)) c->untunable.insert(tkey);
   }
-  Plan pl;
+  Plan pl, fp;
   int rc = choose_plan(c, P, mode, dtype, pl);
   if (rc) return rc;
-  Tables *tb = nullptr;
+  bool fill = choose_fill(c, pl, P, fp);
+  const size_t need = pl.total_bytes + (fill ? (size_t)fp.ncl * fp.slot_bytes : 0);
+  if (fill && need > free_budget(c)) fill = false;
+  Tables *tb = nullptr, *tbf = nullptr;
   rc = get_tables(c, pl.Q, pl.V, &tb);
   if (rc) return rc;
-  rc = ensure_scratch(c, pl.total_bytes);
+  if (fill && (rc = get_tables(c, fp.Q, fp.V, &tbf))) return rc;
+  // (get_tables may grow the table list: look the main table up again)
+  if (fill && (rc = get_tables(c, pl.Q, pl.V, &tb))) return rc;
+  rc = ensure_scratch(c, fill ? need : pl.total_bytes);
   if (rc) return rc;
-  WaveParams wp;
-  rc = fill_params(c, pl, tb, P, wp);
+  WaveParams wp, wpf;
+  rc = fill_params(c, pl, tb, P, wp, nullptr, fill);
   if (rc) return rc;
   wp.P = P; wp.v = v; wp.dobs = dobs; wp.dseis = dseis; wp.seis = seis; wp.grad = grad;
   wp.rho_scale = mode == WM_GRADIENT ? (float)((double)wp.dx2 / (sigma * sigma)) : wp.dx2;
+  if (fill) {
+    if ((rc = fill_params(c, fp, tbf, P, wpf, &pl, true))) return rc;
+    wpf.P = P; wpf.v = v; wpf.dobs = dobs; wpf.dseis = dseis; wpf.seis = seis; wpf.grad = grad;
+    wpf.rho_scale = wp.rho_scale;
+  }
   // graph replay keyed by everything the launch depends on
   uint64_t sigma_bits;
   memcpy(&sigma_bits, &sigma, 8);
@@ -577,10 +679,16 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
       ((uintptr_t)pl.gw << 32) | (uintptr_t)pl.Hb,
       ((uintptr_t)pl.spi << 32) | (uintptr_t)pl.ipp,
       ((uintptr_t)pl.items << 32) | (uintptr_t)pl.nseg,
-      (uintptr_t)pl.smem};
+      (uintptr_t)pl.smem,
+      fill ? (((uintptr_t)fp.Q << 48) | ((uintptr_t)fp.V << 32) | ((uintptr_t)fp.T << 16) |
+              (uintptr_t)fp.ncl)
+           : 0};
+  const Plan *fpp = fill ? &fp : nullptr;
+  const WaveParams *wpfp = fill ? &wpf : nullptr;
   if (!c->use_graphs) {
     if ((rc = prepare_wave(c, pl))) return rc;
-    rc = enqueue_batched(c, pl, wp, P, sigma, misfit, st);
+    if (fill && (rc = prepare_wave(c, fp))) return rc;
+    rc = enqueue_batched(c, pl, wp, P, sigma, misfit, st, fpp, wpfp);
     c->last_stream = st;
     return rc;
   }
@@ -592,9 +700,10 @@ static int run_batched(fwi_ctx *c, int mode, const float *v, int P, const float 
     }
   }
   if ((rc = prepare_wave(c, pl))) return rc;
+  if (fill && (rc = prepare_wave(c, fp))) return rc;
   cudaGraph_t graph;
   VIP_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  rc = enqueue_batched(c, pl, wp, P, sigma, misfit, c->cap_stream);
+  rc = enqueue_batched(c, pl, wp, P, sigma, misfit, c->cap_stream, fpp, wpfp);
   cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
   if (rc) { if (ce == cudaSuccess) cudaGraphDestroy(graph); return rc; }
   VIP_TRY(ce);
@@ -848,8 +957,8 @@ static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *d
     }
   }
   if (mode == WM_GRADIENT && misfit) {
-    j_reduce_kernel<<<idiv_up(P, 128), 128, 0, st>>>(c->pl_J, P, c->S, 1,
-                                                     0.5 / (sigma * sigma), misfit, c->d_status);
+    j_pairs_kernel<<<idiv_up(P, 128), 128, 0, st>>>(c->pl_J, P, c->S, 0.5 / (sigma * sigma),
+                                                    misfit, c->d_status);
     VIP_CHECK_LAUNCH();
   }
   c->last_stream = st;
@@ -944,6 +1053,12 @@ int fwi_create(const fwi_geom *g, size_t workspace_limit_bytes, fwi_ctx **out) {
     return fail(VIP_ERR_CUDA);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(VIP_ERR_CUDA);
+  if (cudaDeviceGetStreamPriorityRange(&c->prio_lo, &c->prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->fill_stream, cudaStreamNonBlocking, c->prio_lo) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(VIP_ERR_CUDA);
   if (const char *e = getenv("VIPGB_GRAPHS")) c->use_graphs = atoi(e) != 0;
   *out = c;
   return VIP_OK;
@@ -963,6 +1078,9 @@ void fwi_destroy(fwi_ctx *c) {
   cudaFree(c->pl_gx); cudaFree(c->pl_recmap); cudaFree(c->pl_J);
   cudaFree(c->d_sub_z); cudaFree(c->d_sub_x); cudaFree(c->d_sub_dobs);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 
@@ -982,6 +1100,28 @@ int fwi_set_plan(fwi_ctx *c, int Q, int V, int T, int sources_per_item, int coef
   c->force_Q = Q; c->force_V = V; c->force_T = T; c->force_spi = sources_per_item;
   c->force_coeff = coeff;
   vip::drop_graphs(c);
+  return VIP_OK;
+}
+
+int fwi_set_fill(fwi_ctx *c, int enable) {
+  if (!c) return VIP_ERR_ARG;
+  c->fill = enable ? 1 : 0;
+  vip::drop_graphs(c);
+  return VIP_OK;
+}
+
+int fwi_query_fill(fwi_ctx *c, int P, int precision, int *fill_out) {
+  if (!c || P < 1 || !fill_out || precision < FWI_FP32 || precision > FWI_CKPT_FP16)
+    return VIP_ERR_ARG;
+  Plan pl, fp;
+  int rc = choose_plan(c, P, WM_GRADIENT, precision, pl);
+  if (rc) return rc;
+  const bool fill = choose_fill(c, pl, P, fp) &&
+                    pl.total_bytes + (size_t)fp.ncl * fp.slot_bytes <= free_budget(c);
+  fill_out[0] = fill ? fp.Q : 0;
+  fill_out[1] = fill ? fp.V : 0;
+  fill_out[2] = fill ? fp.T : 0;
+  fill_out[3] = fill ? fp.ncl : 0;
   return VIP_OK;
 }
 

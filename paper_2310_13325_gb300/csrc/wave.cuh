@@ -78,13 +78,15 @@ struct WaveParams {
   const float *dseis;    // [P][S][R][N]
   float rho_scale;       // dx^2/sigma^2 (gradient) or dx^2 (adjoint)
   float *seis;           // [P][S][R][N]
-  double *Jpart;         // [P*S][Q] sum of squared residuals per CTA
+  double *Jrec;          // [P*S][R] sum of squared residuals per receiver
   float *grad;           // [P][nz][nx]
   int grad_atomic;       // 1 when several work items share a particle: each
                          // item then writes its partial gradient to GI
   float *GI;             // [items][nz][nx] partial gradients (split items)
   int *status;           // bit 0: CFL violation; bit 1: non-finite velocity;
                          // bit 2: non-finite misfit
+  int *work;             // next unclaimed work item, shared by every launch of a
+                         // call (nullptr: cluster c takes items c, c + clusters, ...)
   // per-cluster scratch slots
   void *Dbuf;   size_t Dslot;    // snapshot elements per slot
   float *Dscale; size_t DSslot;  // FP16 scales per slot
@@ -307,7 +309,8 @@ struct StepArgs {
   long long dnext;   // adjoint: element offset of the next step's slab (-1: none)
   int vnext_t;       // sample whose receiver values are fetched in this step (-1: none)
   int vnext_par;     // value slot they go to
-  float *Jf;         // per-thread squared residuals of the last few steps (FP32)
+  float *Jf;         // [4] squared residuals of the last few steps of the thread's
+                     // receivers (FP32), one entry per receiver slot
 };
 
 // Receiver mask type of a task (4 bits per row).
@@ -489,22 +492,27 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
 // (forward modelling) or residuals against the observed sample, parked in
 // value slot (t-1)&1 by the thread that reads it here (gradient). The
 // residual r = d - d_obs and the adjoint source r dx^2/sigma^2 are rounded
-// to FP32 once each; r^2 is summed in FP32 over a few steps (Jf) and then
-// added to the FP64 misfit accumulator by the caller. The adjoint-only mode
-// records nothing.
+// to FP32 once each; r^2 is summed per receiver in FP32 over a few steps
+// (Jf[u] for the thread's u-th receiver) and then added to that receiver's
+// FP64 accumulator by the caller. Each receiver belongs to one band and one
+// thread of it, so its sum does not depend on the launch shape. The
+// adjoint-only mode records nothing.
 template <int MODE>
 __device__ __forceinline__ void record_receivers(const WaveParams &p, const Band &B,
                                                  const float *lev, int t, int pair, int slot,
                                                  float *Jf, int tid, int T) {
   const float *vrec = B.val + ((t - 1) & 1) * p.Rpad;
-  for (int q = tid; q < B.nrb; q += T) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {        // at most 4 receivers per thread (R <= 4 T)
+    const int q = tid + u * T;
+    if (q >= B.nrb) break;
     const int rr = B.rid[q];
     const float d = lev[B.roff[q]];
     if (MODE == WM_FORWARD) {
       p.seis[((size_t)pair * p.R + rr) * p.N + (t - 1)] = d;
     } else if (MODE == WM_GRADIENT) {
       const float res = __fsub_rn(d, vrec[q]);
-      *Jf = __fmaf_rn(res, res, *Jf);
+      Jf[u] = __fmaf_rn(res, res, Jf[u]);
       p.rho[slot * p.rhoslot + (size_t)rr * p.N + (t - 1)] = __fmul_rn(res, p.rho_scale);
     }
   }
@@ -750,7 +758,19 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
   for (int q = tid; q < W4; q += T) B.gxs[q] = p.gx[q];
   const size_t slab = (size_t)p.Q * HW;   // elements of one snapshot
 
-  for (int item = cid; item < p.items; item += ncl) {
+  // Work items: with a shared counter (several launches of one call draw from
+  // it) the cluster's first thread claims the next item and the other CTAs
+  // read it from that CTA's shared memory after a cluster barrier; every item
+  // ends with a cluster barrier, so the next claim cannot overwrite a value a
+  // CTA has not read yet.
+  __shared__ int claimed;
+  auto next_item = [&](int prev) -> int {
+    if (!p.work) return prev < 0 ? cid : prev + ncl;
+    if (b == 0 && tid == 0) claimed = atomicAdd(p.work, 1);
+    cluster.sync();
+    return *cluster.map_shared_rank(&claimed, 0);
+  };
+  for (int item = next_item(-1); item < p.items; item = next_item(item)) {
     const int pp = item / p.ipp;
     const int s0 = (item - pp * p.ipp) * p.spi;
     const int s1 = min(p.S, s0 + p.spi);
@@ -796,15 +816,15 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
       // ---------------- forward sweep
       band_zero(p, B, tid, T);
       step_fence();
-      double jacc = 0.0;
-      float jf = 0.f;
+      double jacc[4] = {0.0, 0.0, 0.0, 0.0};
+      float jf[4] = {0.f, 0.f, 0.f, 0.f};
       int ph = 0;
       bool edge;
       for (int n = 0; n < p.N; ++n) {
         StepArgs a;
         a.ph = ph; a.t = n; a.slot = cid; a.pair = pair; a.s = s;
         a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
-        a.record = MODE != WM_ADJOINT; a.Jf = &jf; a.dnext = -1;
+        a.record = MODE != WM_ADJOINT; a.Jf = jf; a.dnext = -1;
         a.vnext_t = MODE == WM_GRADIENT ? n : -1;
         a.vnext_par = n & 1;
         if (MODE == WM_FORWARD || p.K > 1) {
@@ -822,27 +842,25 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
         }
         step_fence(edge);
         ph ^= 1;
-        if ((n & 15) == 15) { jacc += (double)jf; jf = 0.f; }
+        if ((n & 15) == 15) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) { jacc[u] += (double)jf[u]; jf[u] = 0.f; }
+        }
       }
       // the last level a^N is trace sample N-1
       if (MODE != WM_ADJOINT)
-        record_receivers<MODE>(p, B, ph ? B.U[1] : B.U[0], p.N, pair, cid, &jf, tid, T);
-      jacc += (double)jf;
+        record_receivers<MODE>(p, B, ph ? B.U[1] : B.U[0], p.N, pair, cid, jf, tid, T);
       cluster_wait();
       if (MODE == WM_GRADIENT) {
-        // CTA reduction of the squared residuals (deterministic order)
-        __shared__ double red[32];
-        double v = jacc;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red[tid >> 5] = v;
-        __syncthreads();
-        if (tid == 0) {
-          double t = 0.0;
-          for (int w = 0; w < T / 32; ++w) t += red[w];
-          p.Jpart[(size_t)pair * p.Q + b] = t;
+        // per-receiver sums of squared residuals (FP64)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = tid + u * T;
+          if (q < B.nrb) p.Jrec[(size_t)pair * p.R + B.rid[q]] = jacc[u] + (double)jf[u];
         }
-        __syncthreads();
       }
+      // every thread has read the last level before the next sweep zeroes it
+      __syncthreads();
       if (MODE == WM_FORWARD) continue;
 
       // ---------------- adjoint sweep

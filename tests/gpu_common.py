@@ -12,7 +12,7 @@ def misfit_tolerance(traces, d_obs):
     """Relative tolerance of the misfit J (Eq. 26) against the oracle, derived
     from the FP32 trace bound rel(d) <= 1e-5: J = |r|^2 / (2 sigma^2) with
     r = d - d_obs, so dJ / J = 2 <r, dd> / |r|^2 <= 2 (|d| / |r|) rel(d), plus
-    the reduction's own rounding (64 FP32 partial sums per thread: 4e-6).
+    the reduction's own rounding (FP32 sums over 16 steps per receiver: 4e-6 covers it).
     traces [P, ...] are the oracle's traces of the particles, d_obs the
     observed data they are compared with (broadcast over P)."""
     t = np.asarray(traces, dtype=np.float64).reshape(len(traces), -1)

@@ -3,10 +3,10 @@ the FP64 oracle, through the C ABI.
 
 Tolerances: relative L2 <= 1e-5 for FP32 traces and gradients driven by data
 residuals. The misfit (Eq. 26) rounds each residual to FP32 once (2^-24), sums
-the squares of at most 64 residuals per thread in FP32 (4 receivers x 16
-steps: relative error <= 64 * 2^-24 ~ 3.8e-6) and accumulates those partial
-sums in FP64: the reduction is held to 4e-6 against an FP64 sum of the same
-GPU traces, and its value against the oracle to a tolerance derived per case
+the squares of each receiver's residuals in FP32 over blocks of 16 steps
+(relative error <= 16 * 2^-24 ~ 1e-6) and accumulates those block sums per
+receiver in FP64, then over receivers in a fixed order: the reduction is held
+to 4e-6 against an FP64 sum of the same GPU traces, and its value against the oracle to a tolerance derived per case
 from the trace tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <= 2 (|d| / |r|) rel(d) +
 4e-6, |d| / |r| measured on the oracle's traces (misfit_tolerance).
 Reduced-precision snapshots are measured and held to the bounds stated with
@@ -88,7 +88,7 @@ def test_plain_loop_equals_batched_bit_for_bit():
     assert torch.equal(Sb, Sp)
     assert torch.equal(Gb, Gp)
     # same FP32 residuals; the batched kernel sums their squares in FP32 over
-    # at most 64 terms before the FP64 accumulation (bound 64 * 2^-24)
+    # 16 steps per receiver before the FP64 accumulation (bound 16 * 2^-24)
     assert torch.allclose(Jb, Jp, rtol=4e-6, atol=0)
 
 
@@ -133,10 +133,12 @@ def test_ragged_grid_every_launch_shape_agrees_with_oracle():
         for p in range(3):
             assert rel(G[p], G_ref[p]) <= 1e-5, (Q, Vr, T, co, p, rel(G[p], G_ref[p]))
         assert np.all(np.abs(J.cpu().numpy() - J_ref) <= jtol * J_ref)
+        # gradients and misfits do not depend on the launch shape
         if base is None:
-            base = G
+            base, baseJ = G, J.cpu().numpy()
         else:
             assert np.array_equal(G, base), (Q, Vr, T, co)
+            assert np.array_equal(J.cpu().numpy(), baseJ), (Q, Vr, T, co)
 
 
 def test_autograd_backward_is_the_oracle_adjoint():
