@@ -536,6 +536,7 @@ def run_other_workload(args, torch):
     P = args.particles or (40 if args.workload == "ssvgd" else 64)
     geo, fwi, X0, dobs_h, sigma, lo, hi = build_problem(cfg, max(P, 2000) if args.workload == "ssvgd" else P, 0, dev, vg, torch)
     fwi.set_autotune(not args.no_autotune)
+    fwi.set_fill(not args.no_fill)
     prec = {"fp32": vg.FWI_FP32, "bf16": vg.FWI_CKPT_BF16, "fp16": vg.FWI_CKPT_FP16}[args.precision]
     dobs = torch.tensor(dobs_h, device=dev)
     lo_t = torch.tensor(lo.reshape(-1), dtype=torch.float32, device=dev)
@@ -623,7 +624,7 @@ def run_other_workload(args, torch):
             "config": {"workload": "%s 240x600 grid dx 10 m, 40 src, 400 rec, %d steps dt 0.8 ms, "
                                    "%d gradients per step" % (args.workload, cfg.nt, P),
                        "precision": args.precision, "sources_per_gradient": nsrc_used,
-                       "plan": fwi.query_plan(P, prec)},
+                       "plan": dict(fwi.query_plan(P, prec), fill=fwi.query_fill(P, prec))},
             "gcell_updates_per_s": cu * P / (t_fwi * 1e-3) / 1e9,
             "fwi_ms_per_step": t_fwi, "update_ms_per_step": t_upd,
             "update": ("ssvgd_step n=2000 d=144000, %s kernel" % args.svgd_kernel
