@@ -239,26 +239,29 @@ def test_svgd_step_one_pass_bf16_gram_error_is_bounded(svgd_case):
     assert e_K <= 1e-3
 
 
-def test_fill_launch_on_idle_sms_changes_no_result():
+@pytest.mark.parametrize("K,prec", [(1, vg.FWI_FP32), (7, vg.FWI_CKPT_BF16)])
+def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
     """The benchmark's grid with more work items than 4-CTA clusters: a second
     launch of smaller global-coefficient clusters takes the SMs the main launch
     leaves idle and draws items from the same counter. Traces, gradients and
     misfits equal those of the main launch alone bit for bit, whichever launch
-    computed an item."""
+    computed an item (store-every-step FP32 snapshots, and restart checkpoints
+    every 7 steps with BF16 snapshots)."""
     sub, geo, g, V, d_obs, sigma = _subset_problem("cfg3", [0, 13], 48, nt=300)
     Vt, Dt = _t(V), _t(d_obs)
     out = {}
     for fill in (True, False):
         fwi = vg.Fwi.from_config(sub, geo)
+        fwi.set_mode(vg.FWI_MODE_BATCHED, K)
         fwi.set_fill(fill)
-        shape = fwi.query_fill(48)
+        shape = fwi.query_fill(48, prec)
         if fill:
             print("fill launch:", shape, "main:", fwi.query_plan(48))
             assert shape["clusters"] >= 1 and shape["cluster_ctas"] < 4
         else:
             assert shape["clusters"] == 0
         S = fwi.forward(Vt).clone()
-        J, G = fwi.gradient(Vt, Dt, sigma)
+        J, G = fwi.gradient(Vt, Dt, sigma, precision=prec)
         out[fill] = (S, J.clone(), G.clone())
         assert fwi.last_status() == 0
         fwi.close()
