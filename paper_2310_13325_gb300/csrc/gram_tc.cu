@@ -359,29 +359,42 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
   const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err, wait));
   tc_fence_after();
   // a non-finite input reported by an earlier kernel of the step (*skip):
-  // the particles are left as they were
-  if (done && !*(volatile int *)&abort_flag && !(skip && *skip)) {
+  // the particles are left as they were. The decision is taken for the whole
+  // CTA, since the epilogue below synchronises it.
+  const bool write = __syncthreads_and(done && !*(volatile int *)&abort_flag && !(skip && *skip));
+  if (write) {
+    // the accumulator tile goes through shared memory (the operand ring is
+    // idle once every MMA has completed), [128][129] floats so that both the
+    // row-wise writes from TMEM and the column-wise reads are free of bank
+    // conflicts; the update then walks each row with consecutive lanes on
+    // consecutive coordinates, so X, Xc, q, lo and hi are read and X written
+    // in whole cache lines
+    constexpr int TP = 129;
+    float *tile = reinterpret_cast<float *>(ring);
     const uint32_t lane_base = tacc + ((uint32_t)(warp * 32) << 16);
-    const float rc = row < n ? rcoef[row] : 0.f;
+    const int trow = warp * 32 + lane;
     for (int ch = 0; ch < 4; ++ch) {
       uint32_t r[32];
       tmem_ld32(lane_base + ch * 32, r);   // all lanes take part
-      if (row < n) {
-        const int c0 = tj * 128 + ch * 32;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const int c = c0 + jj;
-          if (c < d) {
-            const size_t g = (size_t)row * d + c;
-            const float xs = q ? Xc[g] * (float)(1.0 / sqrt((double)q[c])) : Xc[g];
-            // the move first (its two parts cancel in part), then one rounding
-            // at the particle's own magnitude
-            float x = X[g] + fmaf(rc, xs, __uint_as_float(r[jj]));
-            if (lo) x = fmaxf(x, lo[c]);
-            if (hi) x = fminf(x, hi[c]);
-            X[g] = x;
-          }
-        }
+      for (int jj = 0; jj < 32; ++jj) tile[trow * TP + ch * 32 + jj] = __uint_as_float(r[jj]);
+    }
+    __syncthreads();
+    for (int rr = warp; rr < 128; rr += 4) {
+      const int i = ti * 128 + rr;
+      if (i >= n) break;
+      const float rc = rcoef[i];
+      for (int cc = lane; cc < 128; cc += 32) {
+        const int c = tj * 128 + cc;
+        if (c >= d) break;
+        const size_t g = (size_t)i * d + c;
+        const float xs = q ? Xc[g] * (float)(1.0 / sqrt((double)q[c])) : Xc[g];
+        // the move first (its two parts cancel in part), then one rounding
+        // at the particle's own magnitude
+        float x = X[g] + fmaf(rc, xs, tile[rr * TP + cc]);
+        if (lo) x = fmaxf(x, lo[c]);
+        if (hi) x = fminf(x, hi[c]);
+        X[g] = x;
       }
     }
   }
