@@ -56,12 +56,15 @@ struct SvgdWs {
   bool tcu;
 };
 
+// Splits of the coordinate axis for the Gram: as many CTAs as fit one wave
+// (two Gram CTAs per SM on the 152 SMs: 97 KB of shared memory and 128 TMEM
+// columns each), never more, so no CTA waits for a second wave.
 static int gram_splits(int n, int d, int gp) {
   const int np = (n + 127) / 128 * 128;
   const int t = np / 128;
   const int tiles = gp == VIP_GRAM_FP32 ? ((n + 63) / 64) * ((n + 63) / 64 + 1) / 2
                                         : t * (t + 1) / 2;
-  int s = (304 + tiles - 1) / tiles;
+  int s = 304 / tiles;
   const int kmax = std::max(1, d / 1024);
   return std::max(1, std::min(s, kmax));
 }
