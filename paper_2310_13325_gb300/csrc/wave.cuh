@@ -456,15 +456,19 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
         const float4 sv = make_float4(s01.x, s01.y, s23.x, s23.y);
         float mul = 1.f;
         if (Snap<DT>::scaled) {
-          float m = c.valid ? fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)),
-                                    fmaxf(fabsf(sv.z), fabsf(sv.w)))
-                            : 0.f;
-          m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-          int e = 0;
-          if (m > 0.f) { frexpf(m, &e); e = 15 - e; }
+          const float m = c.valid ? fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)),
+                                          fmaxf(fabsf(sv.z), fabsf(sv.w)))
+                                  : 0.f;
+          // the warp's largest magnitude (non-negative floats order like
+          // their bit patterns) and its binary exponent E, m = f 2^E with f in
+          // [0.5, 1): E = exponent field - 126; the scale 2^(15 - E) brings the
+          // block's largest value just below 2^15, clamped to 2^(+-120) (a zero
+          // block gets scale 1, a subnormal maximum the largest scale)
+          const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+          int e = mb ? 141 - (int)(mb >> 23) : 0;
           e = max(-120, min(120, e));
-          mul = ldexpf(1.f, e);
-          if ((tid & 31) == 0) Sw[i] = ldexpf(1.f, -e);
+          mul = __int_as_float((e + 127) << 23);
+          if ((tid & 31) == 0) Sw[i] = __int_as_float((127 - e) << 23);
         }
         if (c.valid) Snap<DT>::st(Dtask, (size_t)i * W4, sv, mul);
       } else if (c.valid) {
