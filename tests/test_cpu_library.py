@@ -69,3 +69,18 @@ def test_tomography_argument_checks(lib):
     assert lib.tomo_gradient_sources(None, None, 1, None, None, None, 1, None, None,
                                      None) == -1
     assert lib.tomo_destroy(None) == 0
+
+
+def test_status_fill_and_test_hook_argument_checks(lib):
+    # rejected before any device call
+    assert lib.svgd_status(None, None) == -1
+    assert lib.svgd_status(ctypes.c_void_p(8), None) == -1          # not 256-byte aligned
+    assert lib.fwi_set_fill(None, 1) == -1
+    out = (ctypes.c_int * 4)()
+    assert lib.fwi_query_fill(None, 4, 0, out) == -1
+    assert lib.fwi_bytes_needed(None) == 0
+    assert lib.vip_test_set_wait(-1, 0) == -1
+    assert lib.vip_test_set_wait(0, 2) == -1
+    assert lib.vip_test_set_wait(0, 0) == 0                          # the default restored
+    assert b"non-finite" in lib.vip_strerror(-8)
+    assert b"wait" in lib.vip_strerror(-5)
