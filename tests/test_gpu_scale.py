@@ -267,3 +267,46 @@ def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
         fwi.close()
     for a, b in zip(out[True], out[False]):
         assert torch.equal(a, b)
+
+
+def test_svgd_step_largest_shape_matches_oracle_on_sampled_rows():
+    """svgd_step at the largest workload's size (2000 particles of the 240x600
+    prior, 144,000 coordinates) with the bound reset. With the bandwidth given
+    (h2 > 0 skips the median), the updated particle i needs only the row
+    D2[i, :], so the oracle computes those rows alone for the sampled
+    particles."""
+    cfg = synth.config("cfg5")
+    v = synth.true_model(cfg)
+    lo, hi = synth.prior_bounds(cfg, v)
+    lo, hi = lo.reshape(-1), hi.reshape(-1)
+    n = 2000
+    X = synth.particles_from_prior(lo, hi, n, seed=2).astype(np.float32).astype(np.float64)
+    G = (np.random.default_rng(17).standard_normal(X.shape) * 1e-3).astype(np.float32)
+    G = G.astype(np.float64)
+    rows = [0, 1, 777, 1000, 1998, 1999]
+    D2 = np.zeros((n, n))
+    D2[rows] = osvgd.sqdist_rows(X, rows)
+    h2 = float(np.median(D2[rows])) / (2.0 * np.log(n + 1.0))
+    phi, _, _ = osvgd.svgd_direction_rows(X, -G, rows, D2, h2)
+    eps = 300.0 / np.abs(phi).max()
+    ref, _ = osvgd.svgd_step_rows(X, -G, eps, rows, D2, h2=h2, lo=lo, hi=hi)
+    Xt = _t(X)
+    ws, h2_used = vg.svgd_step(Xt, _t(G), eps, h2=h2, lo=_t(lo), hi=_t(hi),
+                               gram_precision=vg.VIP_GRAM_BF16X3, gscale=-1.0)
+    assert vg.svgd_status(ws) == vg.VIP_OK
+    assert h2_used.item() == pytest.approx(h2, rel=1e-7)
+    got = Xt.double().cpu().numpy()[rows]
+    ex, em = rel(got, ref), rel(got - X[rows], ref - X[rows])
+    # per element, the move may differ by the FP32 rounding of the stored
+    # particle (2^-24 of |x| before and after) plus the FP32 accumulation of
+    # the n particles' terms of Eq. 17, at most (n + 6) 2^-24 times the sum of
+    # their magnitudes A = (eps / n) sum_j k_ij (|G_j| + |x_i - x_j| / h^2)
+    K = osvgd.rbf(D2[rows], h2)
+    A = np.stack([(eps / n) * (K[k] @ np.abs(G) +
+                               (K[k][:, None] * np.abs(X[i][None, :] - X)).sum(axis=0) / h2)
+                  for k, i in enumerate(rows)])
+    bound = 2.0 ** -24 * (np.abs(X[rows]) + np.abs(ref)) + (n + 6) * 2.0 ** -24 * A
+    ratio = (np.abs(got - ref) / bound).max()
+    print("svgd_step 2000 x 144000 (given bandwidth), sampled rows: updated X %.2e, move %.2e, "
+          "largest |error| / per-element bound %.3f" % (ex, em, ratio))
+    assert ex <= 1e-5 and ratio <= 1.0
