@@ -246,7 +246,8 @@ def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
     leaves idle and draws items from the same counter. Traces, gradients and
     misfits equal those of the main launch alone bit for bit, whichever launch
     computed an item (store-every-step FP32 snapshots, and restart checkpoints
-    every 7 steps with BF16 snapshots)."""
+    every 7 steps with BF16 snapshots), in the forward, gradient and adjoint-only
+    modes."""
     sub, geo, g, V, d_obs, sigma = _subset_problem("cfg3", [0, 13], 48, nt=300)
     Vt, Dt = _t(V), _t(d_obs)
     out = {}
@@ -262,7 +263,9 @@ def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
             assert shape["clusters"] == 0
         S = fwi.forward(Vt).clone()
         J, G = fwi.gradient(Vt, Dt, sigma, precision=prec)
-        out[fill] = (S, J.clone(), G.clone())
+        J, G = J.clone(), G.clone()
+        A = fwi.adjoint(Vt, S - Dt[None], precision=prec).clone()   # autograd backward
+        out[fill] = (S, J, G, A)
         assert fwi.last_status() == 0
         fwi.close()
     for a, b in zip(out[True], out[False]):
