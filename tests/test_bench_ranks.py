@@ -1,7 +1,8 @@
 """Multi-rank logic of bench.py on CPU: two gloo ranks (world size 2) agree on
 the slowest rank's time, and the job value counts every rank's particles.
-Each rank of the benchmark runs an independent replica; the only collective
-is this timing reduction."""
+(The ranks' particles are coupled by the update through one all-gather per
+iteration, covered by tests/test_sharded.py; this file covers the timing
+reduction and the launch accounting.)"""
 import os
 import socket
 
@@ -53,4 +54,7 @@ def test_launch_count_of_a_gradient_plan():
     import bench
     assert bench.fwi_gradient_launches({"sources_per_item": 2}, 20) == 3
     assert bench.fwi_gradient_launches({"sources_per_item": 20}, 20) == 2
+    # and the fill launch on the idle SMs when the plan has one
+    fill = {"cluster_ctas": 2, "rows_per_thread": 8, "threads": 288, "clusters": 4}
+    assert bench.fwi_gradient_launches({"sources_per_item": 2, "fill": fill}, 20) == 4
     assert bench.SVGD_STEP_LAUNCHES == 28
