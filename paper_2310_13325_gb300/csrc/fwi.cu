@@ -420,6 +420,10 @@ static void drop_graphs(fwi_ctx *c) {
 static bool choose_fill(fwi_ctx *c, const Plan &mn, int P, Plan &fp) {
   if (!c->fill || c->force_Q || c->force_V || c->force_T || c->force_coeff || c->force_spi)
     return false;
+  // FP16 snapshots share one scale per warp row of 128 cells, and which cells
+  // share a warp depends on the launch shape: items computed by the fill launch
+  // would round differently and make the result depend on the dynamic split
+  if (mn.dtype == FWI_CKPT_FP16 && mn.mode != WM_FORWARD) return false;
   if (mn.items <= mn.ncl) return false;
   const int idle = c->sm_count - mn.Q * mn.ncl;
   if (idle < 2) return false;

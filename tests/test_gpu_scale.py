@@ -246,8 +246,8 @@ def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
     leaves idle and draws items from the same counter. Traces, gradients and
     misfits equal those of the main launch alone bit for bit, whichever launch
     computed an item (store-every-step FP32 snapshots, and restart checkpoints
-    every 7 steps with BF16 snapshots), in the forward, gradient and adjoint-only
-    modes."""
+    every 7 steps with BF16 snapshots), in the forward, gradient, adjoint-only and
+    source-minibatch calls."""
     sub, geo, g, V, d_obs, sigma = _subset_problem("cfg3", [0, 13], 48, nt=300)
     Vt, Dt = _t(V), _t(d_obs)
     out = {}
@@ -265,7 +265,8 @@ def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
         J, G = fwi.gradient(Vt, Dt, sigma, precision=prec)
         J, G = J.clone(), G.clone()
         A = fwi.adjoint(Vt, S - Dt[None], precision=prec).clone()   # autograd backward
-        out[fill] = (S, J, G, A)
+        Jm, Gm = fwi.gradient(Vt, Dt, sigma, precision=prec, sources=[1])   # minibatch
+        out[fill] = (S, J, G, A, Jm.clone(), Gm.clone())
         assert fwi.last_status() == 0
         fwi.close()
     for a, b in zip(out[True], out[False]):
@@ -313,3 +314,18 @@ def test_svgd_step_largest_shape_matches_oracle_on_sampled_rows():
     print("svgd_step 2000 x 144000 (given bandwidth), sampled rows: updated X %.2e, move %.2e, "
           "largest |error| / per-element bound %.3f" % (ex, em, ratio))
     assert ex <= 1e-5 and ratio <= 1.0
+
+
+def test_fp16_snapshot_gradients_have_no_fill_launch():
+    """Scaled FP16 snapshots share one scale per warp row of 128 cells, which the
+    launch shape decides: their gradients never use the fill launch, so they do
+    not depend on which launch computed an item (and repeat bit for bit)."""
+    sub, geo, g, V, d_obs, sigma = _subset_problem("cfg3", [0, 13], 48, nt=300)
+    fwi = vg.Fwi.from_config(sub, geo)
+    assert fwi.query_fill(48, vg.FWI_CKPT_FP16)["clusters"] == 0
+    assert fwi.query_fill(48, vg.FWI_CKPT_BF16)["clusters"] >= 1
+    Vt, Dt = _t(V), _t(d_obs)
+    J1, G1 = fwi.gradient(Vt, Dt, sigma, precision=vg.FWI_CKPT_FP16)
+    J1, G1 = J1.clone(), G1.clone()
+    J2, G2 = fwi.gradient(Vt, Dt, sigma, precision=vg.FWI_CKPT_FP16)
+    assert torch.equal(G1, G2) and torch.equal(J1, J2)
