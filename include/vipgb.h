@@ -93,7 +93,7 @@ typedef struct fwi_ctx fwi_ctx;
  * runs in FP32; restart checkpoints (checkpoint interval > 1) are FP32. */
 #define FWI_FP32       0
 #define FWI_CKPT_BF16  1
-#define FWI_CKPT_FP16  2   /* FP16 with a power-of-two scale per 128 cells */
+#define FWI_CKPT_FP16  2   /* FP16 with a power-of-two scale per row of 4 cells */
 
 /* Execution modes. BATCHED: every (particle, source) pair of a call runs in
  * one persistent thread-block-cluster launch that keeps the wavefields in
@@ -139,11 +139,7 @@ int  fwi_autotune(fwi_ctx *ctx, int P, int precision);
  * does not fit the device makes later calls return VIP_ERR_UNSUPPORTED.
  * Traces and misfits do not depend on the shape; gradients do not depend on
  * Q, V, T or coeff (every cell update and accumulation is evaluated
- * identically) and are deterministic for any split of the sources. The one
- * exception is FWI_CKPT_FP16: its power-of-two scale is shared by the 128
- * cells of one warp's row, which the shape decides, so the gradient changes
- * with the shape within the FP16 rounding bound (and is deterministic for a
- * given shape). */
+ * identically) and are deterministic for any split of the sources. */
 int  fwi_set_plan(fwi_ctx *ctx, int Q, int V, int T, int sources_per_item, int coeff);
 int  fwi_set_autotune(fwi_ctx *ctx, int enable);
 
@@ -155,9 +151,8 @@ int  fwi_set_autotune(fwi_ctx *ctx, int enable);
  * the SMs left idle, at a lower priority, and both launches draw the work
  * items from one counter. Results do not depend on which launch computed an
  * item (every cell update, accumulation and per-receiver misfit sum is
- * evaluated identically). Gradients with FWI_CKPT_FP16 snapshots never fill
- * (their block scales follow the launch shape, see fwi_set_plan).
- * fwi_set_fill(ctx, 0) disables it; forced plans (fwi_set_plan) never fill. fwi_query_fill writes 4 ints to fill_out
+ * evaluated identically). fwi_set_fill(ctx, 0) disables it; forced plans
+ * (fwi_set_plan) never fill. fwi_query_fill writes 4 ints to fill_out
  * (host): {cluster_ctas, rows_per_thread, threads, clusters} of the fill
  * launch a gradient call for P particles would add, or zeros. */
 int  fwi_set_fill(fwi_ctx *ctx, int enable);

@@ -217,7 +217,8 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
   if (grad) {
     const int steps = pl.K == 1 ? c->N : pl.K;
     pl.Dslot = (size_t)steps * slab;
-    if (pl.dtype == FWI_CKPT_FP16) pl.DSslot = (size_t)steps * pl.Q * pl.nwblk * pl.V;
+    // FP16: one scale exponent (a byte) per row of 4 cells
+    if (pl.dtype == FWI_CKPT_FP16) pl.DSslot = (size_t)steps * pl.Q * pl.Hb * pl.NXg;
     pl.GPslot = pl.gw ? 0 : (size_t)c->NZ * c->NX;   // gw: the fold reads the accumulator
     if (pl.mode == WM_GRADIENT) pl.rhoslot = (size_t)c->R * c->N;
     if (pl.K > 1) {
@@ -230,7 +231,7 @@ static void plan_memory(const fwi_ctx *c, Plan &pl, int P) {
   }
   // keep every slot 256-byte aligned
   auto a = [](size_t n, size_t es) { return align_up(n * es, 256); };
-  pl.slot_bytes = a(pl.Dslot, dtype_size(pl.dtype)) + a(pl.DSslot, 4) + a(pl.rhoslot, 4) +
+  pl.slot_bytes = a(pl.Dslot, dtype_size(pl.dtype)) + a(pl.DSslot, 1) + a(pl.rhoslot, 4) +
                   a(pl.GPslot, 4) + a(pl.CKslot, 4) + a(pl.ASslot, 4) + a(pl.Wgslot, 4) +
                   a(pl.Ggslot, 4);
   const size_t gi = (pl.mode != WM_FORWARD && pl.ipp > 1)
@@ -420,10 +421,6 @@ static void drop_graphs(fwi_ctx *c) {
 static bool choose_fill(fwi_ctx *c, const Plan &mn, int P, Plan &fp) {
   if (!c->fill || c->force_Q || c->force_V || c->force_T || c->force_coeff || c->force_spi)
     return false;
-  // FP16 snapshots share one scale per warp row of 128 cells, and which cells
-  // share a warp depends on the launch shape: items computed by the fill launch
-  // would round differently and make the result depend on the dynamic split
-  if (mn.dtype == FWI_CKPT_FP16 && mn.mode != WM_FORWARD) return false;
   if (mn.items <= mn.ncl) return false;
   const int idle = c->sm_count - mn.Q * mn.ncl;
   if (idle < 2) return false;
@@ -556,7 +553,7 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   // slot s occupies [s*slot_bytes, (s+1)*slot_bytes); fields are strided by
   // slot_bytes so that per-slot offsets below are in elements of each field
   wp.Dbuf = sub(pl.Dslot, dtype_size(pl.dtype));
-  wp.Dscale = (float *)sub(pl.DSslot, 4);
+  wp.Dscale = (signed char *)sub(pl.DSslot, 1);
   wp.rho = (float *)sub(pl.rhoslot, 4);
   wp.GP = (float *)sub(pl.GPslot, 4);
   wp.CK = (float *)sub(pl.CKslot, 4);
@@ -565,7 +562,7 @@ static int fill_params(fwi_ctx *c, const Plan &pl, Tables *tb, int P, WaveParams
   wp.Gg = (float *)sub(pl.Ggslot, 4);
   const size_t sb = pl.slot_bytes;
   wp.Dslot = sb / dtype_size(pl.dtype);
-  wp.DSslot = sb / 4; wp.rhoslot = sb / 4; wp.GPslot = sb / 4; wp.CKslot = sb / 4;
+  wp.DSslot = sb; wp.rhoslot = sb / 4; wp.GPslot = sb / 4; wp.CKslot = sb / 4;
   wp.ASslot = sb / 4; wp.Wgslot = sb / 4; wp.Ggslot = sb / 4;
   return cv.ok() ? VIP_OK : VIP_ERR_NOMEM;
 }

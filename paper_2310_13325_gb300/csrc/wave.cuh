@@ -21,7 +21,7 @@
 // D^k = Lh a^{k-1} + f_{k-1} delta_src being the bracketed Laplacian term the
 // forward step already forms (the discrete counterpart of the -2/v^3 u_tt
 // cross-correlation). The forward pass therefore stores D^k (FP32, BF16 or
-// FP16 with a power-of-two scale per 128 cells) and the adjoint pass reads it
+// FP16 with a power-of-two scale per row of a task's 4 cells) and the adjoint pass reads it
 // back; with a restart-checkpoint interval K > 1 only the state every K steps
 // is stored and each K-step segment is recomputed before its adjoint sweep.
 //
@@ -89,7 +89,7 @@ struct WaveParams {
                          // call (nullptr: cluster c takes items c, c + clusters, ...)
   // per-cluster scratch slots
   void *Dbuf;   size_t Dslot;    // snapshot elements per slot
-  float *Dscale; size_t DSslot;  // FP16 scales per slot
+  signed char *Dscale; size_t DSslot;  // FP16 scale exponents per slot (one per 4 cells)
   float *rho;   size_t rhoslot;  // [R][N] adjoint sources per slot
   float *GP;    size_t GPslot;   // [NZ][NX] gradient gather per slot
   float *CK;    size_t CKslot;   // restart checkpoints per slot
@@ -305,7 +305,7 @@ struct StepArgs {
   float src_val;
   bool record;       // forward: record the current level at the receivers
   size_t dofs;       // element offset of this step's snapshot slab
-  size_t sofs;       // offset of this step's scale slab
+  size_t sofs;       // offset of this step's scale slab (FP16: [Q][Hb][NXg] bytes)
   long long dnext;   // adjoint: element offset of the next step's slab (-1: none)
   int vnext_t;       // sample whose receiver values are fetched in this step (-1: none)
   int vnext_par;     // value slot they go to
@@ -349,7 +349,8 @@ __device__ __forceinline__ void add_lane(float2 &s01, float2 &s23, int j, float 
 template <int V, bool ADJ, bool SNAP, int MODE, class DT, bool GW>
 __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
                                           typename MaskT<V>::type rm, DT *Dtask,
-                                          const DT *Dnext, const float *Stask, float *Sw,
+                                          const DT *Dnext, const signed char *Stask,
+                                          signed char *Sw,
                                           const float *vcur, int PX, int dn, int dW, int dG,
                                           const float *wg, float *gg, int W4, float2 k1,
                                           float2 k2, float2 k3, float2 k4, int tid) {
@@ -369,7 +370,7 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
   if (ADJ && SNAP) {
 #pragma unroll
     for (int i = 0; i < kAhead && i < V; ++i) {
-      dinv[i] = Snap<DT>::scaled ? Stask[i] : 1.f;
+      dinv[i] = Snap<DT>::scaled ? __int_as_float((127 - Stask[i * (W4 >> 2)]) << 23) : 1.f;
       dq[i] = Snap<DT>::ld(Dtask, (size_t)i * W4, 1.f);
     }
   }
@@ -385,7 +386,8 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
 #pragma unroll
   for (int i = 0; i < V; ++i) {
     if (ADJ && SNAP && i + kAhead < V) {
-      dinv[i + kAhead] = Snap<DT>::scaled ? Stask[i + kAhead] : 1.f;
+      dinv[i + kAhead] =
+          Snap<DT>::scaled ? __int_as_float((127 - Stask[(i + kAhead) * (W4 >> 2)]) << 23) : 1.f;
       dq[i + kAhead] = Snap<DT>::ld(Dtask, (size_t)(i + kAhead) * W4, 1.f);
     }
     if (GW && i + kAhead < V) {
@@ -456,19 +458,18 @@ __device__ __forceinline__ void task_rows(const StepArgs &a, const TaskCtx &c,
         const float4 sv = make_float4(s01.x, s01.y, s23.x, s23.y);
         float mul = 1.f;
         if (Snap<DT>::scaled) {
-          const float m = c.valid ? fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)),
-                                          fmaxf(fabsf(sv.z), fabsf(sv.w)))
-                                  : 0.f;
-          // the warp's largest magnitude (non-negative floats order like
-          // their bit patterns) and its binary exponent E, m = f 2^E with f in
-          // [0.5, 1): E = exponent field - 126; the scale 2^(15 - E) brings the
-          // block's largest value just below 2^15, clamped to 2^(+-120) (a zero
-          // block gets scale 1, a subnormal maximum the largest scale)
-          const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+          // one power-of-two scale per row of the task's 4 cells: the largest
+          // magnitude m and its binary exponent E (m = f 2^E, f in [0.5, 1):
+          // E = exponent field - 126; non-negative floats order like their
+          // bit patterns); the scale 2^(15 - E) brings the largest value just
+          // below 2^15, clamped to 2^(+-120) (zero cells get scale 1, a
+          // subnormal maximum the largest scale); its exponent is stored
+          const float m = fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)), fmaxf(fabsf(sv.z), fabsf(sv.w)));
+          const unsigned mb = __float_as_uint(m);
           int e = mb ? 141 - (int)(mb >> 23) : 0;
           e = max(-120, min(120, e));
           mul = __int_as_float((e + 127) << 23);
-          if ((tid & 31) == 0) Sw[i] = __int_as_float((127 - e) << 23);
+          if (c.valid) Sw[i * (W4 >> 2)] = (signed char)e;
         }
         if (c.valid) Snap<DT>::st(Dtask, (size_t)i * W4, sv, mul);
       } else if (c.valid) {
@@ -565,7 +566,7 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
   DT *Dp = reinterpret_cast<DT *>(p.Dbuf) + a.slot * p.Dslot + a.dofs;
   const DT *Dn = a.dnext >= 0 ? reinterpret_cast<const DT *>(p.Dbuf) + a.slot * p.Dslot + a.dnext
                               : nullptr;
-  float *Sp = Snap<DT>::scaled ? p.Dscale + a.slot * p.DSslot + a.sofs : nullptr;
+  signed char *Sp = Snap<DT>::scaled ? p.Dscale + a.slot * p.DSslot + a.sofs : nullptr;
   const float *vcur = B.val + (a.t & 1) * p.Rpad;
   if (!ADJ && a.record && a.t >= 1)
     record_receivers<MODE>(p, B, cur, a.t, a.pair, a.slot, a.Jf, tid, T);
@@ -596,8 +597,6 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
   const float2 k3 = make_float2(p.c3, p.c3), k4 = make_float2(p.c4, p.c4);
   const int nstrip = Hb / V;
   const int nin = (nstrip > 2 ? nstrip - 2 : 0) * NXg;   // tasks of the inner strips
-  // the FP16 snapshot scale is a warp-wide maximum: every lane takes part
-  constexpr bool all_lanes = Snap<DT>::scaled && !ADJ && SNAP;
   bool waited = false;
   for (int task0 = tid; task0 < p.ntask_pad; task0 += T) {
     // warp-uniform: the warp's 32 consecutive tasks reach the edge strips
@@ -607,7 +606,7 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
     }
     TaskCtx c;
     c.valid = task0 < p.ntask;
-    if (!all_lanes && !c.valid) break;
+    if (!c.valid) break;
     const int t = c.valid ? task0 : p.ntask - 1;
     int sp, cgp;
     if (t < nin) {
@@ -651,8 +650,9 @@ __device__ __forceinline__ bool band_step(const WaveParams &p, const Band &B,
     const size_t toff = (size_t)r0 * W4 + gcol;
     DT *Dt = Dp + toff;
     const DT *Dnt = Dn ? Dn + toff : nullptr;
-    const float *St = Sp ? Sp + (task0 / 32) * V : nullptr;
-    float *Sw = Sp ? Sp + (task0 / 32) * V : nullptr;
+    // FP16 scale exponents of the task's rows: one byte per row of its 4 cells
+    const signed char *St = Sp ? Sp + (size_t)r0 * NXg + cgp : nullptr;
+    signed char *Sw = Sp ? Sp + (size_t)r0 * NXg + cgp : nullptr;
     task_rows<V, ADJ, SNAP, MODE, DT, GW>(a, c, rm, Dt, Dnt, St, Sw, vcur, PX, dn, dW, dG,
                                           GW ? Wgb + toff : nullptr,
                                           (GW && ADJ) ? Ggb + toff : nullptr, W4, k1, k2, k3,
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
           edge = band_step<V, false, false, MODE, DT, GW>(p, B, a, tid, T);
         } else {
           a.dofs = (size_t)n * slab + (size_t)b * HW;
-          a.sofs = ((size_t)n * p.Q + b) * p.nwblk * V;
+          a.sofs = ((size_t)n * p.Q + b) * p.Hb * p.NXg;
           edge = band_step<V, false, true, MODE, DT, GW>(p, B, a, tid, T);
         }
         step_fence(edge);
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
           a.ph = ph; a.t = k; a.slot = cid; a.pair = pair; a.s = s;
           a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jf = nullptr;
           a.dofs = (size_t)(k - 1) * slab + (size_t)b * HW;
-          a.sofs = ((size_t)(k - 1) * p.Q + b) * p.nwblk * V;
+          a.sofs = ((size_t)(k - 1) * p.Q + b) * p.Hb * p.NXg;
           a.dnext = k >= 2 ? (long long)((size_t)(k - 2) * slab + (size_t)b * HW) : -1;
           a.vnext_t = k >= 2 ? k - 2 : -1;
           a.vnext_par = (k - 1) & 1;
@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
             a.src_task = src_task; a.src_bit = src_bit; a.src_val = __ldg(&p.wavelet[n]);
             a.record = false; a.Jf = nullptr; a.dnext = -1; a.vnext_t = -1; a.vnext_par = 0;
             a.dofs = (size_t)(n - n0) * slab + (size_t)b * HW;
-            a.sofs = ((size_t)(n - n0) * p.Q + b) * p.nwblk * V;
+            a.sofs = ((size_t)(n - n0) * p.Q + b) * p.Hb * p.NXg;
             step_fence(band_step<V, false, true, MODE, DT, GW>(p, B, a, tid, T));
             fph ^= 1;
           }
@@ -918,7 +918,7 @@ __global__ void __launch_bounds__(WaveMaxThreads<V, GW>::value, 1)
             a.ph = ph; a.t = k; a.slot = cid; a.pair = pair; a.s = s;
             a.src_task = -1; a.src_bit = 0; a.src_val = 0.f; a.record = false; a.Jf = nullptr;
             a.dofs = (size_t)(k - 1 - n0) * slab + (size_t)b * HW;
-            a.sofs = ((size_t)(k - 1 - n0) * p.Q + b) * p.nwblk * V;
+            a.sofs = ((size_t)(k - 1 - n0) * p.Q + b) * p.Hb * p.NXg;
             a.dnext = k - 2 >= n0 ? (long long)((size_t)(k - 2 - n0) * slab + (size_t)b * HW)
                                   : -1;
             a.vnext_t = k - 1 > n0 ? k - 2 : -1;

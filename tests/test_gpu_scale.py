@@ -239,15 +239,17 @@ def test_svgd_step_one_pass_bf16_gram_error_is_bounded(svgd_case):
     assert e_K <= 1e-3
 
 
-@pytest.mark.parametrize("K,prec", [(1, vg.FWI_FP32), (7, vg.FWI_CKPT_BF16)])
+@pytest.mark.parametrize("K,prec", [(1, vg.FWI_FP32), (7, vg.FWI_CKPT_BF16),
+                                    (1, vg.FWI_CKPT_FP16), (7, vg.FWI_CKPT_FP16)])
 def test_fill_launch_on_idle_sms_changes_no_result(K, prec):
     """The benchmark's grid with more work items than 4-CTA clusters: a second
     launch of smaller global-coefficient clusters takes the SMs the main launch
     leaves idle and draws items from the same counter. Traces, gradients and
     misfits equal those of the main launch alone bit for bit, whichever launch
     computed an item (store-every-step FP32 snapshots, and restart checkpoints
-    every 7 steps with BF16 snapshots), in the forward, gradient, adjoint-only and
-    source-minibatch calls."""
+    every 7 steps with BF16 snapshots, scaled FP16 snapshots, whose power-of-two
+    scale belongs to the 4 cells of a task's row whatever the launch shape), in
+    the forward, gradient, adjoint-only and source-minibatch calls."""
     sub, geo, g, V, d_obs, sigma = _subset_problem("cfg3", [0, 13], 48, nt=300)
     Vt, Dt = _t(V), _t(d_obs)
     out = {}
@@ -314,18 +316,3 @@ def test_svgd_step_largest_shape_matches_oracle_on_sampled_rows():
     print("svgd_step 2000 x 144000 (given bandwidth), sampled rows: updated X %.2e, move %.2e, "
           "largest |error| / per-element bound %.3f" % (ex, em, ratio))
     assert ex <= 1e-5 and ratio <= 1.0
-
-
-def test_fp16_snapshot_gradients_have_no_fill_launch():
-    """Scaled FP16 snapshots share one scale per warp row of 128 cells, which the
-    launch shape decides: their gradients never use the fill launch, so they do
-    not depend on which launch computed an item (and repeat bit for bit)."""
-    sub, geo, g, V, d_obs, sigma = _subset_problem("cfg3", [0, 13], 48, nt=300)
-    fwi = vg.Fwi.from_config(sub, geo)
-    assert fwi.query_fill(48, vg.FWI_CKPT_FP16)["clusters"] == 0
-    assert fwi.query_fill(48, vg.FWI_CKPT_BF16)["clusters"] >= 1
-    Vt, Dt = _t(V), _t(d_obs)
-    J1, G1 = fwi.gradient(Vt, Dt, sigma, precision=vg.FWI_CKPT_FP16)
-    J1, G1 = J1.clone(), G1.clone()
-    J2, G2 = fwi.gradient(Vt, Dt, sigma, precision=vg.FWI_CKPT_FP16)
-    assert torch.equal(G1, G2) and torch.equal(J1, J2)
