@@ -373,9 +373,10 @@ def plain_rate(cfg, v1, dobs, sigma, vg, torch):
 
 
 # Kernels one svgd_step enqueues (three-piece BF16 Gram, tensor-core update):
-# centre, norms, gram_tc, d2_finish, median_init, 8 x median_hist, 8 x
-# median_select, bandwidth, kbar, split_a, split_b, rcoef, update_tc, poison.
-SVGD_STEP_LAUNCHES = 28
+# centre, norms, gram_tc, d2_finish, median_init, 8 x median_hist (each radix
+# pass selects its digit in its last block), bandwidth, kbar, split_a,
+# split_b, rcoef, update_tc, poison.
+SVGD_STEP_LAUNCHES = 20
 
 
 def fwi_gradient_launches(plan, nsrc):

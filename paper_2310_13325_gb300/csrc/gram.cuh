@@ -18,16 +18,17 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
                    int n, int dp, int np, int splits, float *parts, int *err, cudaStream_t st);
 
 // SVGD / sSVGD update on the tensor cores: X[i][c] <- clip(X[i][c] +
-// sum_k A[i][k] B[c][k] + rcoef[i] Xc[i][c] / sqrt(q_c), lo, hi) for i < n,
-// c < d, with A [np][Kp] and B [dp][Kp] each given as three BF16 pieces
-// (h, m, l) multiplied with the six-product split (FP32-class accuracy).
-// np, dp multiples of 128, Kp of 64; q, lo, hi may be NULL. err as for
+// sum_k A[i][k] B[c][k] + rcoef[i] Xc[i][c] isq[c], lo, hi) for i < n, c < d,
+// with A [np][Kp] and B [dp][Kp] each given as three BF16 pieces (h, m, l)
+// multiplied with the six-product split (FP32-class accuracy), and isq[c] =
+// 1/sqrt(q_c) of the matrix-valued kernel (FP32). np, dp multiples of 128,
+// Kp of 64; isq, lo, hi may be NULL (no scaling, no bound). err as for
 // gram_tc_launch. skip (device word, may be NULL): when nonzero at the time
 // the kernel runs, X is left unchanged (an earlier kernel of the step saw a
 // non-finite input).
 int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const B[3], int n,
                      int d, int np, int dp, int Kp, const float *Xc, const float *rcoef,
-                     const float *q, const float *lo, const float *hi, float *X, int *err,
+                     const float *isq, const float *lo, const float *hi, float *X, int *err,
                      const int *skip, cudaStream_t st);
 
 }  // namespace vip

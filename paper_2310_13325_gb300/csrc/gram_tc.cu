@@ -279,15 +279,16 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
 // columns: the matching right-hand sides), both as three BF16 pieces and the
 // six-product split, the same pipeline as gram_tc_kernel over all 6 * KB
 // blocks, then applies the update in the epilogue:
-//   X[i][c] = clip(X[i][c] + D[i][c] + rcoef[i] Xc[i][c] / sqrt(q_c), lo, hi)
-// (q NULL: 1). Tiles are ordered with the particle tiles of one coordinate
-// tile adjacent, so its B rows are read once into L2.
+//   X[i][c] = clip(X[i][c] + D[i][c] + rcoef[i] Xc[i][c] isq[c], lo, hi)
+// with isq[c] = 1/sqrt(q_c) of the matrix-valued kernel (isq NULL: 1). Tiles
+// are ordered with the particle tiles of one coordinate tile adjacent, so its
+// B rows are read once into L2.
 __global__ void __launch_bounds__(128, 1) update_tc_kernel(
     const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap am,
     const __grid_constant__ CUtensorMap al, const __grid_constant__ CUtensorMap bh,
     const __grid_constant__ CUtensorMap bm, const __grid_constant__ CUtensorMap bl, int KB,
     int MT, int n, int d, const float *__restrict__ Xc, const float *__restrict__ rcoef,
-    const float *__restrict__ q, const float *__restrict__ lo, const float *__restrict__ hi,
+    const float *__restrict__ isq, const float *__restrict__ lo, const float *__restrict__ hi,
     float *X, int *err, const int *skip, long long wait, int stall) {
   extern __shared__ __align__(1024) uint8_t usm_raw[];
   uint8_t *ring = (uint8_t *)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
@@ -380,21 +381,50 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
       for (int jj = 0; jj < 32; ++jj) tile[trow * TP + ch * 32 + jj] = __uint_as_float(r[jj]);
     }
     __syncthreads();
-    for (int rr = warp; rr < 128; rr += 4) {
-      const int i = ti * 128 + rr;
-      if (i >= n) break;
-      const float rc = rcoef[i];
-      for (int cc = lane; cc < 128; cc += 32) {
-        const int c = tj * 128 + cc;
-        if (c >= d) break;
-        const size_t g = (size_t)i * d + c;
-        const float xs = q ? Xc[g] * (float)(1.0 / sqrt((double)q[c])) : Xc[g];
-        // the move first (its two parts cancel in part), then one rounding
-        // at the particle's own magnitude
-        float x = X[g] + fmaf(rc, xs, tile[rr * TP + cc]);
-        if (lo) x = fmaxf(x, lo[c]);
-        if (hi) x = fminf(x, hi[c]);
-        X[g] = x;
+    // Each lane owns the tile columns lane + 32 k (k < 4) of the rows its warp
+    // walks (warp, warp + 4, ...): their column terms are read once, and the
+    // rows go in groups of kRows so that a thread has 2 kRows x 4 loads of X
+    // and Xc in flight at a time instead of one pair per DRAM round trip.
+    constexpr int kRows = 4;
+    int cidx[4];
+    float cs[4], clo[4], chi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = tj * 128 + lane + 32 * k;
+      cidx[k] = c < d ? c : -1;
+      cs[k] = (isq && c < d) ? isq[c] : 1.f;
+      clo[k] = (lo && c < d) ? lo[c] : 0.f;
+      chi[k] = (hi && c < d) ? hi[c] : 0.f;
+    }
+    for (int m0 = 0; m0 < 32; m0 += kRows) {
+      float xv[kRows][4], xcv[kRows][4], rc[kRows];
+#pragma unroll
+      for (int t = 0; t < kRows; ++t) {
+        const int i = ti * 128 + warp + 4 * (m0 + t);
+        rc[t] = i < n ? rcoef[i] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool ok = i < n && cidx[k] >= 0;
+          const size_t g = (size_t)i * d + cidx[k];
+          xv[t][k] = ok ? X[g] : 0.f;
+          xcv[t][k] = ok ? Xc[g] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kRows; ++t) {
+        const int rr = warp + 4 * (m0 + t);
+        const int i = ti * 128 + rr;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (i >= n || cidx[k] < 0) continue;
+          const float xs = isq ? xcv[t][k] * cs[k] : xcv[t][k];
+          // the move first (its two parts cancel in part), then one rounding
+          // at the particle's own magnitude
+          float x = xv[t][k] + fmaf(rc[t], xs, tile[rr * TP + lane + 32 * k]);
+          if (lo) x = fmaxf(x, clo[k]);
+          if (hi) x = fminf(x, chi[k]);
+          X[(size_t)i * d + cidx[k]] = x;
+        }
       }
     }
   }
@@ -462,7 +492,7 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
 
 int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const Bm[3], int n,
                      int d, int np, int dp, int Kp, const float *Xc, const float *rcoef,
-                     const float *q, const float *lo, const float *hi, float *X, int *err,
+                     const float *isq, const float *lo, const float *hi, float *X, int *err,
                      const int *skip, cudaStream_t st) {
   if (np % 128 || dp % 128 || Kp % 64 || n > np || d > dp) return VIP_ERR_ARG;
   for (int k = 0; k < 3; ++k)
@@ -480,7 +510,7 @@ int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const
                                (int)smem));
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   update_tc_kernel<<<MT * NT, 128, smem, st>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], Kp / 64,
-                                               MT, n, d, Xc, rcoef, q, lo, hi, X, err, skip,
+                                               MT, n, d, Xc, rcoef, isq, lo, hi, X, err, skip,
                                                g_wait_cycles, g_stall_producer);
   VIP_CHECK_LAUNCH();
   return VIP_OK;

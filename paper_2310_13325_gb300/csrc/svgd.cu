@@ -1,10 +1,11 @@
 // SVGD (Eq. 13-17) and stochastic SVGD (Eq. 21-25) particle updates.
 //
 // Pipeline of one step on X [n][d], G [n][d] (all kernels below):
-//   1. centre      mean over particles (FP64), Xc = X - mean (FP32) and its
-//                  BF16 image (one piece, or the three-piece split
+//   1. centre      mean over particles (FP64-class: compensated FP32 sums
+//                  per thread, FP64 across threads), Xc = X - mean (FP32) and
+//                  its BF16 image (one piece, or the three-piece split
 //                  xc ~ h + m + l for FP32-class accuracy)
-//   2. norms       |xc_i|^2 in FP64
+//   2. norms       |xc_i|^2, FP64-class the same way
 //   3. gram        partial Xc Xc^T over K-splits (tcgen05 BF16 tensor cores,
 //                  or a SIMT FP32 reference path)
 //   4. finish      D2_ij = |xc_i|^2 + |xc_j|^2 - 2 Gram_ij in FP64, clamped at
@@ -19,6 +20,13 @@
 // The repulsive term uses the identity sum_j k_ij (m_i - m_j) =
 // r_i xc_i - (Kbar Xc)_i, exact in real arithmetic because the particle
 // mean cancels; centring keeps it well conditioned in FP32.
+//
+// FP64 runs at a small fraction of the FP32 rate on this GPU (conversions
+// between float and double included), so no step does FP64 arithmetic per
+// element of X: per-element sums use error-free FP32 transformations (the
+// compensated summation and dot product of Ogita, Rump and Oishi, 2005), and
+// FP64 only combines the per-thread partial sums and forms the per-pair
+// distances of step 4.
 //
 // Diagonal matrix-valued kernel K_Q = Q^{-1} k_Q, Q = diag(q) (Discussion
 // section): step 1 stores the centred particles scaled by sqrt(q), so steps
@@ -36,9 +44,11 @@ namespace vip {
 
 struct SvgdWs {
   double *mean;
+  float *qf;   // [2][dp] matrix-valued kernel: 1/q_c and 1/sqrt(q_c) per column (FP32)
   float *Xc;
   __nv_bfloat16 *Xh, *Xm, *Xl;   // BF16 pieces: x ~ h + m + l
   double *nrm;
+  unsigned int *done;       // blocks of a radix-pass histogram that have finished
   float *parts;
   double *D2;
   unsigned long long *keys;
@@ -80,12 +90,14 @@ static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base,
   w.splits = gram_splits(n, d, gp);
   w.M = n * (n - 1) / 2;
   w.mean = cv.take<double>(d);
+  w.qf = cv.take<float>((size_t)2 * w.dp);
   w.Xc = cv.take<float>((size_t)n * d);
   const bool tc = gp != VIP_GRAM_FP32;
   w.Xh = cv.take<__nv_bfloat16>(tc ? (size_t)w.np * w.dp : 0);
   w.Xm = cv.take<__nv_bfloat16>(tc && gp == VIP_GRAM_BF16X3 ? (size_t)w.np * w.dp : 0);
   w.Xl = cv.take<__nv_bfloat16>(tc && gp == VIP_GRAM_BF16X3 ? (size_t)w.np * w.dp : 0);
   w.nrm = cv.take<double>(n);
+  w.done = cv.take<unsigned int>(1);
   w.parts = cv.take<float>((size_t)w.splits * w.np * w.np);
   w.D2 = cv.take<double>((size_t)n * n);
   w.keys = cv.take<unsigned long long>(std::max(w.M, 1));
@@ -109,29 +121,106 @@ static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base,
 }
 
 // ---------------------------------------------------------------------------
-__global__ void centre_kernel(const float *__restrict__ X, const float *__restrict__ q, int n,
-                              int d, int dp, int np, double *mean, float *Xc, __nv_bfloat16 *Xh,
-                              __nv_bfloat16 *Xm, __nv_bfloat16 *Xl, int *nonfinite) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= dp) return;
+// Error-free transformations in FP32: s + e == a + b exactly (Knuth's
+// TwoSum) and p + e == a * b exactly (the product's rounding error from one
+// FMA). Every operation is rounded explicitly, so none is contracted.
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+  return s;
+}
+
+// Compensated running sum (s, c): s the FP32 sum, c the accumulated rounding
+// errors; s + c carries about twice the FP32 precision (Sum2 / Dot2 of
+// Ogita, Rump and Oishi): the error of (double)s + (double)c is at most
+// gamma_m^2 times the sum of magnitudes for m terms, gamma_m ~ m 2^-24.
+struct Comp {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    s = two_sum(s, x, e);
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = __fmul_rn(x, x);
+    const float pe = __fmaf_rn(x, x, -p);
+    float e;
+    s = two_sum(s, p, e);
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Column means and the centred particles. A block owns 32 columns: its 8
+// warps sum interleaved sets of rows of them (each warp reads whole 128-byte
+// row segments) with compensated FP32 sums, the 8 partial sums of a column
+// are added in FP64 in a fixed order (so the mean does not depend on timing),
+// and then the warps write the centred rows, FP32 Xc and its BF16 pieces.
+// Xc = x - m is formed from the mean held as two floats mh + ml: x - mh
+// exactly (TwoSum), then one rounding of its sum with -ml, which is within
+// 2^-48 |m| of the exact difference. With the matrix-valued kernel (q
+// given) the columns are scaled by sqrt(q_c) in FP64 as before, and 1/q_c
+// and 1/sqrt(q_c) are kept in FP32 for the update, which then needs no FP64
+// division per element.
+constexpr int kCentreRows = 8;
+__global__ void __launch_bounds__(32 * kCentreRows) centre_kernel(
+    const float *__restrict__ X, const float *__restrict__ q, int n, int d, int dp, int np,
+    double *mean, float *Xc, __nv_bfloat16 *Xh, __nv_bfloat16 *Xm, __nv_bfloat16 *Xl,
+    float *qf, int *nonfinite) {
+  __shared__ double part[kCentreRows][32];
+  __shared__ double mcol[32], scol[32];
+  __shared__ float mhc[32], mlc[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
+  const bool live = c < d;
+  Comp acc;
+  if (live)
+    for (int i = ty; i < n; i += kCentreRows) acc.add(X[(size_t)i * d + c]);
+  part[ty][tx] = acc.value();
+  __syncthreads();
+  if (ty == 0 && live) {
+    double t = 0.0;
+    for (int r = 0; r < kCentreRows; ++r) t += part[r][tx];
+    if (!isfinite(t)) atomicOr(nonfinite, 1);   // a NaN or infinity in the column
+    const double m = t / n;
+    mean[c] = m;
+    mcol[tx] = m;
+    const float mh = (float)m;
+    mhc[tx] = mh;
+    mlc[tx] = (float)(m - (double)mh);
+    const double sq = q ? sqrt((double)q[c]) : 1.0;   // Q-metric scale of the column
+    scol[tx] = sq;
+    if (q) {
+      qf[c] = (float)(1.0 / (double)q[c]);
+      qf[dp + c] = (float)(1.0 / sq);
+    }
+  }
+  __syncthreads();
+  const int nblk = (d + 31) / 32;   // blocks holding live columns
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-  if (c >= d) {
-    for (int i = 0; i < np; ++i) {
+  if ((int)blockIdx.x >= nblk) {    // padding columns only
+    for (int i = ty; i < np; i += kCentreRows) {
       if (Xh) Xh[(size_t)i * dp + c] = z;
       if (Xm) { Xm[(size_t)i * dp + c] = z; Xl[(size_t)i * dp + c] = z; }
     }
     return;
   }
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * d + c];
-  if (!isfinite(s)) atomicOr(nonfinite, 1);   // a NaN or infinity in the column
-  const double m = s / n;
-  mean[c] = m;
-  const double sq = q ? sqrt((double)q[c]) : 1.0;   // Q-metric scale of the column
-  for (int i = 0; i < n; ++i) {
-    const float xc = q ? (float)(((double)X[(size_t)i * d + c] - m) * sq)
-                       : (float)((double)X[(size_t)i * d + c] - m);
-    Xc[(size_t)i * d + c] = xc;
+  const double m = live ? mcol[tx] : 0.0, sq = live ? scol[tx] : 1.0;
+  const float nmh = live ? -mhc[tx] : 0.f, ml = live ? mlc[tx] : 0.f;
+  for (int i = ty; i < n; i += kCentreRows) {
+    const size_t g = (size_t)i * d + c;
+    float xc = 0.f;
+    if (live) {
+      if (q) {
+        xc = (float)(((double)X[g] - m) * sq);
+      } else {
+        float e;
+        const float s = two_sum(X[g], nmh, e);
+        xc = __fadd_rn(s, __fsub_rn(e, ml));
+      }
+      Xc[g] = xc;
+    }
     if (Xh) {
       // three-piece BF16 split: each remainder is exact in FP32
       const __nv_bfloat16 h = __float2bfloat16_rn(xc);
@@ -145,7 +234,7 @@ __global__ void centre_kernel(const float *__restrict__ X, const float *__restri
     }
   }
   if (Xh)
-    for (int i = n; i < np; ++i) {
+    for (int i = n + ty; i < np; i += kCentreRows) {
       Xh[(size_t)i * dp + c] = z;
       if (Xm) { Xm[(size_t)i * dp + c] = z; Xl[(size_t)i * dp + c] = z; }
     }
@@ -178,15 +267,26 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return t;
 }
 
+// |xc_i|^2: a compensated FP32 dot product per thread (16-byte loads where
+// the rows are 16-byte aligned), the threads' sums added in FP64.
 __global__ void norms_kernel(const float *__restrict__ Xc, int d, double *nrm) {
   __shared__ double red[32];
   const int i = blockIdx.x;
-  double s = 0.0;
-  for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    const double v = Xc[(size_t)i * d + c];
-    s += v * v;
+  const float *row = Xc + (size_t)i * d;
+  Comp acc;
+  if ((d & 3) == 0) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+    for (int c = threadIdx.x; c < d / 4; c += blockDim.x) {
+      const float4 v = r4[c];
+      acc.add_sq(v.x);
+      acc.add_sq(v.y);
+      acc.add_sq(v.z);
+      acc.add_sq(v.w);
+    }
+  } else {
+    for (int c = threadIdx.x; c < d; c += blockDim.x) acc.add_sq(row[c]);
   }
-  const double t = block_sum(s, red);
+  const double t = block_sum(acc.value(), red);
   if (threadIdx.x == 0) nrm[i] = t;
 }
 
@@ -252,7 +352,8 @@ __global__ void d2_finish_kernel(const float *__restrict__ parts, int splits, in
 
 // Radix selection of up to two ranks of the multiset {n zeros} U {each upper
 // D2 value twice}. sel: [0..1] prefix, [2] mask, [3..4] rank, [5..6] zero flag.
-__global__ void median_init_kernel(int n, unsigned long long *sel, unsigned int *hist) {
+__global__ void median_init_kernel(int n, unsigned long long *sel, unsigned int *hist,
+                                   unsigned int *done) {
   const long long N2 = (long long)n * n;
   long long kf[2];
   if (N2 % 2 == 0) { kf[0] = N2 / 2 - 1; kf[1] = N2 / 2; }
@@ -265,11 +366,60 @@ __global__ void median_init_kernel(int n, unsigned long long *sel, unsigned int 
   }
   sel[2] = 0ull;
   for (int q = 0; q < 512; ++q) hist[q] = 0u;
+  *done = 0u;
 }
 
+// Digit selection of one radix pass, by one warp: lane l holds the counts of
+// digits 8l .. 8l+7; a warp prefix sum over the lanes' totals finds the lane
+// whose digits contain rank k, and that lane walks its eight. The histogram
+// is cleared for the next pass by all lanes. The counts are read from L2,
+// where the other blocks' atomics went.
+__device__ void median_select_warp(int shift, unsigned long long *sel, unsigned int *hist) {
+  const int l = threadIdx.x & 31;
+  for (int r = 0; r < 2; ++r) {
+    if (sel[5 + r]) continue;   // warp-uniform
+    const unsigned long long k = sel[3 + r];
+    unsigned int cnt[8];
+    unsigned long long tot = 0ull;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      cnt[j] = __ldcg(&hist[r * 256 + 8 * l + j]);
+      tot += cnt[j];
+    }
+    unsigned long long incl = tot;   // inclusive prefix over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (l >= o) incl += v;
+    }
+    const unsigned long long excl = incl - tot;
+    if (k >= excl && k < incl) {
+      unsigned long long cum = excl;
+      for (int j = 0; j < 8; ++j) {
+        if (k < cum + cnt[j]) {
+          sel[r] |= (unsigned long long)(8 * l + j) << shift;
+          sel[3 + r] = k - cum;
+          break;
+        }
+        cum += cnt[j];
+      }
+    }
+    __syncwarp();
+  }
+  if (l == 0) sel[2] |= 255ull << shift;
+  __syncwarp();
+  for (int q = l; q < 512; q += 32) hist[q] = 0u;
+}
+
+// One radix pass: histogram of the 8-bit digit at shift of the keys that
+// match the prefix selected so far, for both target ranks. The last block to
+// finish (a counter taken after a memory fence) then selects the digits, so
+// a pass is one launch.
 __global__ void median_hist_kernel(const unsigned long long *__restrict__ keys, int M, int shift,
-                                   const unsigned long long *sel, unsigned int *hist) {
+                                   unsigned long long *sel, unsigned int *hist,
+                                   unsigned int *done) {
   __shared__ unsigned int h[512];
+  __shared__ bool last;
   for (int q = threadIdx.x; q < 512; q += blockDim.x) h[q] = 0u;
   __syncthreads();
   const unsigned long long mask = sel[2], p0 = sel[0], p1 = sel[1];
@@ -283,25 +433,14 @@ __global__ void median_hist_kernel(const unsigned long long *__restrict__ keys, 
   __syncthreads();
   for (int q = threadIdx.x; q < 512; q += blockDim.x)
     if (h[q]) atomicAdd(&hist[q], h[q]);
-}
-
-__global__ void median_select_kernel(int shift, unsigned long long *sel, unsigned int *hist) {
-  if (threadIdx.x != 0) return;
-  for (int r = 0; r < 2; ++r) {
-    if (sel[5 + r]) continue;
-    unsigned long long k = sel[3 + r], cum = 0ull;
-    for (int dg = 0; dg < 256; ++dg) {
-      const unsigned long long c = hist[r * 256 + dg];
-      if (k < cum + c) {
-        sel[r] |= (unsigned long long)dg << shift;
-        sel[3 + r] = k - cum;
-        break;
-      }
-      cum += c;
-    }
-  }
-  sel[2] |= 255ull << shift;
-  for (int q = 0; q < 512; ++q) hist[q] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) median_select_warp(shift, sel, hist);
+  if (threadIdx.x == 0) *done = 0u;
 }
 
 __global__ void bandwidth_kernel(int n, const unsigned long long *sel, float h2_user,
@@ -318,6 +457,7 @@ __global__ void bandwidth_kernel(int n, const unsigned long long *sel, float h2_
     v = med < 1e-30 ? 1.0 : med / (2.0 * log((double)n + 1.0));
   }
   h2[0] = v;
+  h2[1] = (double)(float)(1.0 / v);   // 1/h^2 in FP32 for the update kernels
   if (h2_out) h2_out[0] = v;
 }
 
@@ -471,48 +611,60 @@ __global__ void split_a_kernel(const float *__restrict__ K, const float *__restr
 }
 
 // Operand B, [dp][Kp] (coordinates x particles, a transpose through shared
-// memory): column k < n holds Y_kc = (eps/n) (gscale G_kc / q_c -
+// memory in 64 x 64 tiles, so that every warp reads 256 contiguous bytes of
+// a particle row and writes 128 contiguous bytes of each piece's coordinate
+// row): column k < n holds Y_kc = (eps/n) (gscale G_kc / q_c -
 // Xc_kc / (sqrt(q_c) h^2)), columns n..2n-1 (sSVGD) Z = noise_scale Xi / sqrt(q_c).
-__global__ void split_b_kernel(const float *__restrict__ G, const float *__restrict__ Xc,
-                               const float *__restrict__ Xi, const double *h2p,
-                               const float *__restrict__ q, int n, int d, int dp, int Kp,
-                               float en, float gscale, float ns, __nv_bfloat16 *Bh,
-                               __nv_bfloat16 *Bm, __nv_bfloat16 *Bl, int *nonfinite) {
-  __shared__ float tile[32][33];
+constexpr int kSplitTile = 64;
+__global__ void __launch_bounds__(256) split_b_kernel(
+    const float *__restrict__ G, const float *__restrict__ Xc, const float *__restrict__ Xi,
+    const double *h2p, const float *__restrict__ iqc, const float *__restrict__ isqc, int n,
+    int d, int dp, int Kp, float en, float gscale, float ns, __nv_bfloat16 *Bh,
+    __nv_bfloat16 *Bm, __nv_bfloat16 *Bl, int *nonfinite) {
+  __shared__ float tile[kSplitTile][kSplitTile + 1];
   bool bad = false;
-  const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  const float inv_h2 = (float)(1.0 / h2p[0]);
-  for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
-    const int k = k0 + kk, c = c0 + threadIdx.x;
-    float v = 0.f;
-    if (c < d) {
-      const double qc = q ? (double)q[c] : 1.0;
-      const float iq = q ? (float)(1.0 / qc) : 1.f, isq = q ? (float)(1.0 / sqrt(qc)) : 1.f;
-      if (k < n) {
-        const size_t g = (size_t)k * d + c;
-        const float gv = G[g];
-        bad |= !isfinite(gv);
-        v = en * (gscale * iq * gv - isq * inv_h2 * Xc[g]);
-      } else if (Xi && k < 2 * n) {
-        v = ns * isq * Xi[(size_t)(k - n) * d + c];
+  const int c0 = blockIdx.x * kSplitTile, k0 = blockIdx.y * kSplitTile;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float inv_h2 = (float)h2p[1];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int cc = tx + 32 * h, c = c0 + cc;
+    // per-column factors of the matrix-valued kernel (1 without it)
+    const float iq = (iqc && c < d) ? iqc[c] : 1.f, isq = (isqc && c < d) ? isqc[c] : 1.f;
+    for (int kk = ty; kk < kSplitTile; kk += 8) {
+      const int k = k0 + kk;
+      float v = 0.f;
+      if (c < d) {
+        if (k < n) {
+          const size_t g = (size_t)k * d + c;
+          const float gv = G[g];
+          bad |= !isfinite(gv);
+          v = en * (gscale * iq * gv - isq * inv_h2 * Xc[g]);
+        } else if (Xi && k < 2 * n) {
+          v = ns * isq * Xi[(size_t)(k - n) * d + c];
+        }
       }
+      tile[kk][cc] = v;
     }
-    tile[kk][threadIdx.x] = v;
   }
   if (bad) atomicOr(nonfinite, 2);
   __syncthreads();
-  for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
-    const int c = c0 + cc, k = k0 + threadIdx.x;
-    if (c < dp && k < Kp) {
-      const size_t o = (size_t)c * Kp + k;
-      split3(tile[threadIdx.x][cc], Bh[o], Bm[o], Bl[o]);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int kk = tx + 32 * h, k = k0 + kk;
+    for (int cc = ty; cc < kSplitTile; cc += 8) {
+      const int c = c0 + cc;
+      if (c < dp && k < Kp) {
+        const size_t o = (size_t)c * Kp + k;
+        split3(tile[kk][cc], Bh[o], Bm[o], Bl[o]);
+      }
     }
   }
 }
 
 __global__ void rcoef_kernel(const float *rs, const double *h2p, int n, float en, float *rc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) rc[i] = en * rs[i] * (float)(1.0 / h2p[0]);
+  if (i < n) rc[i] = en * rs[i] * (float)h2p[1];
 }
 
 // A bounded wait of the tensor-core update gave up: its tiles are unknown,
@@ -532,7 +684,8 @@ __global__ void __launch_bounds__(256) update_kernel(
     const float *__restrict__ K, const float *__restrict__ G, const float *__restrict__ Xc,
     const float *__restrict__ Lk, const float *__restrict__ Xi, const float *__restrict__ rs,
     const double *h2p, int n, int d, float eps, float gscale, float noise_scale,
-    const float *__restrict__ q, const float *lo, const float *hi, float *X, int *nonfinite) {
+    const float *__restrict__ iqc, const float *__restrict__ isqc, const float *lo,
+    const float *hi, float *X, int *nonfinite) {
   constexpr int BK = 16;
   bool bad = false;
   __shared__ float Ks[BK][64], Ls[NOISE ? BK : 1][64];
@@ -580,7 +733,7 @@ __global__ void __launch_bounds__(256) update_kernel(
     __syncthreads();
   }
   if (bad) atomicOr(nonfinite, 2);
-  const float inv_h2 = (float)(1.0 / h2p[0]);
+  const float inv_h2 = (float)h2p[1];
   const float inv_n = 1.f / (float)n;
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + ty * 4 + u;
@@ -591,7 +744,7 @@ __global__ void __launch_bounds__(256) update_kernel(
       if (c >= d) continue;
       const size_t g = (size_t)i * d + c;
       float x;
-      if (!q) {
+      if (!iqc) {
         const float rep = (fmaf(ri, Xc[g], -a2[u][v])) * inv_h2;
         const float phi = fmaf(gscale, a1[u][v], rep) * inv_n;
         x = fmaf(eps, phi, X[g]);
@@ -599,8 +752,7 @@ __global__ void __launch_bounds__(256) update_kernel(
       } else {
         // matrix-valued kernel: Q^{-1} on the driving term, Q^{-1/2} on the
         // repulsion (built from sqrt(q)-scaled Xc) and on the noise
-        const double qc = (double)q[c];
-        const float iq = (float)(1.0 / qc), isq = (float)(1.0 / sqrt(qc));
+        const float iq = iqc[c], isq = isqc[c];
         const float rep = (fmaf(ri, Xc[g], -a2[u][v])) * inv_h2 * isq;
         const float phi = fmaf(gscale * iq, a1[u][v], rep) * inv_n;
         x = fmaf(eps, phi, X[g]);
@@ -619,9 +771,10 @@ static int distances(const float *X, const float *q, int n, int d, float h2, int
   const bool tc = gp != VIP_GRAM_FP32;
   const bool x3 = gp == VIP_GRAM_BF16X3;
   VIP_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), st));
-  centre_kernel<<<idiv_up(w.dp, 128), 128, 0, st>>>(X, q, n, d, w.dp, w.np, w.mean, w.Xc,
-                                                    tc ? w.Xh : nullptr, x3 ? w.Xm : nullptr,
-                                                    x3 ? w.Xl : nullptr, w.flag + 3);
+  centre_kernel<<<w.dp / 32, 32 * kCentreRows, 0, st>>>(X, q, n, d, w.dp, w.np, w.mean, w.Xc,
+                                                        tc ? w.Xh : nullptr,
+                                                        x3 ? w.Xm : nullptr,
+                                                        x3 ? w.Xl : nullptr, w.qf, w.flag + 3);
   VIP_CHECK_LAUNCH();
   norms_kernel<<<n, 256, 0, st>>>(w.Xc, d, w.nrm);
   VIP_CHECK_LAUNCH();
@@ -640,14 +793,12 @@ static int distances(const float *X, const float *q, int n, int d, float h2, int
                                                              w.D2, w.keys);
   VIP_CHECK_LAUNCH();
   if (!(h2 > 0.f)) {
-    median_init_kernel<<<1, 1, 0, st>>>(n, w.sel, w.hist);
+    median_init_kernel<<<1, 1, 0, st>>>(n, w.sel, w.hist, w.done);
     VIP_CHECK_LAUNCH();
     if (w.M > 0) {
       const int blocks = std::min(1024, std::max(1, idiv_up(w.M, 256 * 8)));
       for (int shift = 56; shift >= 0; shift -= 8) {
-        median_hist_kernel<<<blocks, 256, 0, st>>>(w.keys, w.M, shift, w.sel, w.hist);
-        VIP_CHECK_LAUNCH();
-        median_select_kernel<<<1, 32, 0, st>>>(shift, w.sel, w.hist);
+        median_hist_kernel<<<blocks, 256, 0, st>>>(w.keys, w.M, shift, w.sel, w.hist, w.done);
         VIP_CHECK_LAUNCH();
       }
     }
@@ -684,14 +835,14 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
   auto tc_update = [&](const float *Lk, const float *noise, float ns) -> int {
     split_a_kernel<<<1024, 256, 0, st>>>(w.K, Lk, n, w.unp, w.uKp, w.Ua[0], w.Ua[1], w.Ua[2]);
     VIP_CHECK_LAUNCH();
-    split_b_kernel<<<dim3(w.udp / 32, w.uKp / 32), dim3(32, 8), 0, st>>>(
-        G, w.Xc, noise, w.h2, q, n, d, w.udp, w.uKp, en, gscale, ns, w.Ub[0], w.Ub[1], w.Ub[2],
-        w.flag + 3);
+    split_b_kernel<<<dim3(w.udp / kSplitTile, w.uKp / kSplitTile), 256, 0, st>>>(
+        G, w.Xc, noise, w.h2, q ? w.qf : nullptr, q ? w.qf + w.dp : nullptr, n, d, w.udp,
+        w.uKp, en, gscale, ns, w.Ub[0], w.Ub[1], w.Ub[2], w.flag + 3);
     VIP_CHECK_LAUNCH();
     rcoef_kernel<<<idiv_up(n, 256), 256, 0, st>>>(w.rs, w.h2, n, en, w.rcoef);
     VIP_CHECK_LAUNCH();
-    int rc2 = update_tc_launch(w.Ua, w.Ub, n, d, w.unp, w.udp, w.uKp, w.Xc, w.rcoef, q, lo, hi,
-                               X, w.flag + 2, w.flag + 3, st);
+    int rc2 = update_tc_launch(w.Ua, w.Ub, n, d, w.unp, w.udp, w.uKp, w.Xc, w.rcoef,
+                               q ? w.qf + w.dp : nullptr, lo, hi, X, w.flag + 2, w.flag + 3, st);
     if (rc2) return rc2;
     poison_kernel<<<1024, 256, 0, st>>>(w.flag + 2, (size_t)n * d, X);
     VIP_CHECK_LAUNCH();
@@ -700,7 +851,8 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
   if (!stochastic && w.tcu) return tc_update(nullptr, nullptr, 0.f);
   if (!stochastic) {
     update_kernel<false><<<ug, 256, 0, st>>>(w.K, G, w.Xc, nullptr, nullptr, w.rs, w.h2, n, d,
-                                             eps, gscale, 0.f, q, lo, hi, X, w.flag + 3);
+                                             eps, gscale, 0.f, q ? w.qf : nullptr,
+                                             q ? w.qf + w.dp : nullptr, lo, hi, X, w.flag + 3);
     VIP_CHECK_LAUNCH();
     return VIP_OK;
   }
@@ -750,7 +902,8 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
     return VIP_OK;
   }
   update_kernel<true><<<ug, 256, 0, st>>>(w.K, G, w.Xc, w.Lk, noise, w.rs, w.h2, n, d, eps, gscale,
-                                          ns, q, lo, hi, X, w.flag + 3);
+                                          ns, q ? w.qf : nullptr, q ? w.qf + w.dp : nullptr, lo,
+                                          hi, X, w.flag + 3);
   VIP_CHECK_LAUNCH();
   // tau is a host local: make the asynchronous copy complete before return
   if (tau_used) VIP_TRY(cudaStreamSynchronize(st));

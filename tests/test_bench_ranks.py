@@ -57,4 +57,4 @@ def test_launch_count_of_a_gradient_plan():
     # and the fill launch on the idle SMs when the plan has one
     fill = {"cluster_ctas": 2, "rows_per_thread": 8, "threads": 288, "clusters": 4}
     assert bench.fwi_gradient_launches({"sources_per_item": 2, "fill": fill}, 20) == 4
-    assert bench.SVGD_STEP_LAUNCHES == 28
+    assert bench.SVGD_STEP_LAUNCHES == 20
