@@ -4,7 +4,13 @@
 // of 64-wide coordinate blocks:
 //   - thread 0 issues TMA tile loads (128 rows x 64 BF16 = 128 B per row,
 //     128-byte swizzle) of the row block i and the row block j into a
-//     3-stage shared-memory ring, signalling a "full" mbarrier per stage;
+//     shared-memory ring, signalling a "full" mbarrier per stage. With the
+//     three-piece split a stage holds all three pieces of both row blocks
+//     (96 KB) and all six products of the split are issued from it, so each
+//     piece is read from L2 once per coordinate block; the ring is then one
+//     stage, and the two CTAs that share an SM overlap one's copies and
+//     epilogue with the other's products. One-piece BF16 stages (32 KB) form
+//     a 3-stage ring;
 //   - thread 32 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M=128,
 //     N=128, K=16, both operands K-major) into a 128-column TMEM accumulator
 //     and releases each stage with tcgen05.commit on its "empty" mbarrier;
@@ -24,10 +30,17 @@
 
 namespace vip {
 
-constexpr int GT_STAGES = 3;
 constexpr int GT_TILE_BYTES = 128 * 64 * 2;           // one operand tile
-constexpr int GT_STAGE_BYTES = 2 * GT_TILE_BYTES;     // A and B
+constexpr int GT_MAX_STAGES = 3;
 constexpr long long GT_WAIT_CYCLES = 2000000000ll;    // ~1 s at 2 GHz
+
+// Ring shape for P operand pieces: stages of 2P tiles (A pieces, then B
+// pieces); one 96 KB stage for P = 3, three 32 KB stages for P = 1.
+template <int P> struct Ring {
+  static constexpr int kStages = P == 3 ? 1 : 3;
+  static constexpr int kStageBytes = 2 * P * GT_TILE_BYTES;
+  static constexpr int kBytes = kStages * kStageBytes;
+};
 
 // Test hook state (host): the wait bound passed to the next launches and
 // whether their producers issue no copies.
@@ -76,10 +89,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err
 
 // After an abort: wait (bounded) until every stage's last issued copy has
 // landed, so no bulk copy into this CTA's shared memory is left in flight.
+// Stage s was last filled by load number s + NST * floor((issued-1-s)/NST).
+template <int NST>
 __device__ __forceinline__ void drain_issued(uint64_t *full_bar, int issued, int *err,
                                              long long limit) {
-  for (int s = 0; s < GT_STAGES && s < issued; ++s) {
-    const int use = (issued - 1 - s) / GT_STAGES;   // last use of stage s issued
+  for (int s = 0; s < NST && s < issued; ++s) {
+    const int use = (issued - 1 - s) / NST;   // last use of stage s issued
     mbar_wait(&full_bar[s], (uint32_t)(use & 1), err, limit);
   }
 }
@@ -152,21 +167,80 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Pass p of the split product uses pieces (A, B) = (kPassA[p], kPassB[p])
-// with 0 = h, 1 = m, 2 = l: hh, hm, mh, hl, lh, mm.
-__constant__ int kPassA[6] = {0, 0, 1, 0, 2, 1};
-__constant__ int kPassB[6] = {0, 1, 0, 2, 0, 1};
+// Product p of the split uses pieces (A, B) = (pass_a(p), pass_b(p)) with
+// 0 = h, 1 = m, 2 = l: hh, hm, mh, hl, lh, mm (the dropped ml, lm, ll are
+// below FP32 resolution).
+__host__ __device__ constexpr int pass_a(int p) { return p == 2 ? 1 : (p == 4 ? 2 : (p == 5 ? 1 : 0)); }
+__host__ __device__ constexpr int pass_b(int p) { return p == 1 ? 1 : (p == 3 ? 2 : (p == 5 ? 1 : 0)); }
+static_assert(pass_a(0) == 0 && pass_a(1) == 0 && pass_a(2) == 1 && pass_a(3) == 0 &&
+                  pass_a(4) == 2 && pass_a(5) == 1 && pass_b(0) == 0 && pass_b(1) == 1 &&
+                  pass_b(2) == 0 && pass_b(3) == 2 && pass_b(4) == 0 && pass_b(5) == 1,
+              "products hh, hm, mh, hl, lh, mm");
 
+// Copy producer (thread 0) and MMA issuer (thread 32) of one CTA over the
+// coordinate blocks kb0 .. kb1-1: per block one stage with the P pieces of
+// row block ya of A and of row block yb of B, and the P == 3 ? 6 : 1 products
+// accumulated into tacc. On an expired wait the thread sets *abort_flag and
+// stops; the producer counts its issued loads in *n_issued.
+template <int P>
+__device__ __forceinline__ void tc_mainloop(const CUtensorMap *const ma[3],
+                                            const CUtensorMap *const mb[3], int ya, int yb,
+                                            int kb0, int kb1, uint8_t *ring, uint64_t *full_bar,
+                                            uint64_t *empty_bar, uint64_t *done_bar,
+                                            uint32_t tacc, int *abort_flag, int *n_issued,
+                                            int *err, long long wait, int stall) {
+  using R = Ring<P>;
+  const int n_iter = kb1 - kb0;
+  if (threadIdx.x == 0) {
+    // producer (with the test hook's stall it issues nothing)
+    for (int i = 0; i < (stall ? 0 : n_iter); ++i) {
+      const int s = i % R::kStages;
+      const uint32_t use = (uint32_t)(i / R::kStages);
+      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err, wait)) { *abort_flag = 1; break; }
+      if (*(volatile int *)abort_flag) break;
+      const int kb = kb0 + i;
+      uint8_t *st = ring + s * R::kStageBytes;
+      mbar_expect_tx(&full_bar[s], R::kStageBytes);
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        tma_load_2d(st + k * GT_TILE_BYTES, ma[k], &full_bar[s], kb * 64, ya * 128);
+        tma_load_2d(st + (P + k) * GT_TILE_BYTES, mb[k], &full_bar[s], kb * 64, yb * 128);
+      }
+      *n_issued = i + 1;
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    for (int i = 0; i < n_iter; ++i) {
+      const int s = i % R::kStages;
+      const uint32_t use = (uint32_t)(i / R::kStages);
+      if (!mbar_wait(&full_bar[s], use & 1u, err, wait)) { *abort_flag = 1; break; }
+      tc_fence_after();
+      const uint32_t st = su32(ring + s * R::kStageBytes);
+#pragma unroll
+      for (int pr = 0; pr < (P == 3 ? 6 : 1); ++pr) {
+        const uint32_t sa = st + pass_a(pr) * GT_TILE_BYTES;
+        const uint32_t sb = st + (P + pass_b(pr)) * GT_TILE_BYTES;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          umma(tacc, sdesc(sa + k * 32), sdesc(sb + k * 32),
+               (i > 0 || pr > 0 || k > 0) ? 1u : 0u);
+      }
+      umma_commit(&empty_bar[s]);
+    }
+    umma_commit(done_bar);
+  }
+}
+
+template <int P>
 __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap mh,
                                                          const __grid_constant__ CUtensorMap mm,
                                                          const __grid_constant__ CUtensorMap ml,
-                                                         int KB, int kper, int total, int np,
-                                                         float *parts, int *err,
-                                                         long long wait, int stall) {
+                                                         int KB, int kper, int np, float *parts,
+                                                         int *err, long long wait, int stall) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
   uint8_t *ring = (uint8_t *)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], done_bar;
+  __shared__ uint64_t full_bar[GT_MAX_STAGES], empty_bar[GT_MAX_STAGES], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, n_issued;
 
@@ -175,19 +249,19 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
   const int T = np / 128;
   while (t >= T - ti) { t -= T - ti; ++ti; }
   const int tj = ti + t;
-  const int g0 = blockIdx.y * kper, g1 = min(total, g0 + kper);
-  float *P = parts + (size_t)blockIdx.y * np * np;
+  const int kb0 = blockIdx.y * kper, kb1 = min(KB, kb0 + kper);
+  float *Pt = parts + (size_t)blockIdx.y * np * np;
   const int row = ti * 128 + warp * 32 + lane;
 
-  if (g0 >= g1) {   // empty coordinate range: the partial tile is zero
+  if (kb0 >= kb1) {   // empty coordinate range: the partial tile is zero
     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 *dst = reinterpret_cast<float4 *>(P + (size_t)row * np + tj * 128);
+    float4 *dst = reinterpret_cast<float4 *>(Pt + (size_t)row * np + tj * 128);
     for (int c = 0; c < 32; ++c) dst[c] = z;
     return;
   }
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < GT_STAGES; ++s) {
+    for (int s = 0; s < Ring<P>::kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -209,49 +283,16 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
   tc_fence_after();
   const uint32_t tacc = tmem_base;
 
-  const int n_iter = g1 - g0;
-  if (threadIdx.x == 0) {
-    // producer (with the test hook's stall it issues nothing)
-    for (int i = 0; i < (stall ? 0 : n_iter); ++i) {
-      const int s = i % GT_STAGES;
-      const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err, wait)) { abort_flag = 1; break; }
-      if (*(volatile int *)&abort_flag) break;
-      const int g = g0 + i;
-      const int pass = g / KB, kb = g - pass * KB;
-      const int pa = kPassA[pass], pb = kPassB[pass];
-      const CUtensorMap *ma = pa == 0 ? &mh : (pa == 1 ? &mm : &ml);
-      const CUtensorMap *mb = pb == 0 ? &mh : (pb == 1 ? &mm : &ml);
-      uint8_t *sa = ring + s * GT_STAGE_BYTES;
-      uint8_t *sb = sa + GT_TILE_BYTES;
-      mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
-      tma_load_2d(sa, ma, &full_bar[s], kb * 64, ti * 128);
-      tma_load_2d(sb, mb, &full_bar[s], kb * 64, tj * 128);
-      n_issued = i + 1;
-    }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer
-    for (int i = 0; i < n_iter; ++i) {
-      const int s = i % GT_STAGES;
-      const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&full_bar[s], use & 1u, err, wait)) { abort_flag = 1; break; }
-      tc_fence_after();
-      const uint32_t sa = su32(ring + s * GT_STAGE_BYTES);
-      const uint32_t sb = sa + GT_TILE_BYTES;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        umma(tacc, sdesc(sa + k * 32), sdesc(sb + k * 32), (i > 0 || k > 0) ? 1u : 0u);
-      umma_commit(&empty_bar[s]);
-    }
-    umma_commit(&done_bar);
-  }
+  const CUtensorMap *const maps[3] = {&mh, &mm, &ml};
+  tc_mainloop<P>(maps, maps, ti, tj, kb0, kb1, ring, full_bar, empty_bar, &done_bar, tacc,
+                 &abort_flag, &n_issued, err, wait, stall);
   __syncwarp();
   // epilogue: wait for the accumulator
   const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err, wait));
   tc_fence_after();
   if (done && !*(volatile int *)&abort_flag) {
     const uint32_t lane_base = tacc + ((uint32_t)(warp * 32) << 16);
-    float *dst = P + (size_t)row * np + tj * 128;
+    float *dst = Pt + (size_t)row * np + tj * 128;
     for (int c = 0; c < 4; ++c) {
       uint32_t r[32];
       tmem_ld32(lane_base + c * 32, r);
@@ -263,7 +304,7 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
     }
   }
   // drain: every stage's copies must have landed before the CTA retires
-  if (threadIdx.x == 0 && abort_flag) drain_issued(full_bar, n_issued, err, wait);
+  if (threadIdx.x == 0 && abort_flag) drain_issued<Ring<P>::kStages>(full_bar, n_issued, err, wait);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -277,8 +318,9 @@ __global__ void __launch_bounds__(128, 1) gram_tc_kernel(const __grid_constant__
 // of D = A B^T with A [np][Kp] (rows: particles; columns: the kernel matrix
 // and, for sSVGD, the Cholesky factor) and B [dp][Kp] (rows: coordinates;
 // columns: the matching right-hand sides), both as three BF16 pieces and the
-// six-product split, the same pipeline as gram_tc_kernel over all 6 * KB
-// blocks, then applies the update in the epilogue:
+// six-product split, the same pipeline as gram_tc_kernel (one 96 KB stage of
+// all six tiles per block of K) over all KB blocks, then applies the update
+// in the epilogue:
 //   X[i][c] = clip(X[i][c] + D[i][c] + rcoef[i] Xc[i][c] isq[c], lo, hi)
 // with isq[c] = 1/sqrt(q_c) of the matrix-valued kernel (isq NULL: 1). Tiles
 // are ordered with the particle tiles of one coordinate tile adjacent, so its
@@ -292,16 +334,15 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
     float *X, int *err, const int *skip, long long wait, int stall) {
   extern __shared__ __align__(1024) uint8_t usm_raw[];
   uint8_t *ring = (uint8_t *)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], done_bar;
+  __shared__ uint64_t full_bar[GT_MAX_STAGES], empty_bar[GT_MAX_STAGES], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, n_issued;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ti = blockIdx.x % MT, tj = blockIdx.x / MT;
-  const int row = ti * 128 + warp * 32 + lane;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < GT_STAGES; ++s) {
+    for (int s = 0; s < Ring<3>::kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -323,39 +364,10 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
   tc_fence_after();
   const uint32_t tacc = tmem_base;
 
-  const int n_iter = 6 * KB;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < (stall ? 0 : n_iter); ++i) {
-      const int s = i % GT_STAGES;
-      const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&empty_bar[s], (use & 1u) ^ 1u, err, wait)) { abort_flag = 1; break; }
-      if (*(volatile int *)&abort_flag) break;
-      const int pass = i / KB, kb = i - pass * KB;
-      const int pa = kPassA[pass], pb = kPassB[pass];
-      const CUtensorMap *ma = pa == 0 ? &ah : (pa == 1 ? &am : &al);
-      const CUtensorMap *mb = pb == 0 ? &bh : (pb == 1 ? &bm : &bl);
-      uint8_t *sa = ring + s * GT_STAGE_BYTES;
-      uint8_t *sb = sa + GT_TILE_BYTES;
-      mbar_expect_tx(&full_bar[s], GT_STAGE_BYTES);
-      tma_load_2d(sa, ma, &full_bar[s], kb * 64, ti * 128);
-      tma_load_2d(sb, mb, &full_bar[s], kb * 64, tj * 128);
-      n_issued = i + 1;
-    }
-  } else if (threadIdx.x == 32) {
-    for (int i = 0; i < n_iter; ++i) {
-      const int s = i % GT_STAGES;
-      const uint32_t use = (uint32_t)(i / GT_STAGES);
-      if (!mbar_wait(&full_bar[s], use & 1u, err, wait)) { abort_flag = 1; break; }
-      tc_fence_after();
-      const uint32_t sa = su32(ring + s * GT_STAGE_BYTES);
-      const uint32_t sb = sa + GT_TILE_BYTES;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        umma(tacc, sdesc(sa + k * 32), sdesc(sb + k * 32), (i > 0 || k > 0) ? 1u : 0u);
-      umma_commit(&empty_bar[s]);
-    }
-    umma_commit(&done_bar);
-  }
+  const CUtensorMap *const mas[3] = {&ah, &am, &al};
+  const CUtensorMap *const mbs[3] = {&bh, &bm, &bl};
+  tc_mainloop<3>(mas, mbs, ti, tj, 0, KB, ring, full_bar, empty_bar, &done_bar, tacc,
+                 &abort_flag, &n_issued, err, wait, stall);
   __syncwarp();
   const bool done = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, err, wait));
   tc_fence_after();
@@ -428,7 +440,7 @@ __global__ void __launch_bounds__(128, 1) update_tc_kernel(
       }
     }
   }
-  if (threadIdx.x == 0 && abort_flag) drain_issued(full_bar, n_issued, err, wait);
+  if (threadIdx.x == 0 && abort_flag) drain_issued<Ring<3>::kStages>(full_bar, n_issued, err, wait);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -478,14 +490,23 @@ int gram_tc_launch(const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xm, const __nv_
   const int T = np / 128;
   const int tiles = T * (T + 1) / 2;
   const int KB = dp / 64;
-  const int total = KB * (Xm ? 6 : 1);
-  const int kper = (total + splits - 1) / splits;
-  const size_t smem = (size_t)GT_STAGES * GT_STAGE_BYTES + 1024;
-  VIP_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+  const int kper = (KB + splits - 1) / splits;
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-  gram_tc_kernel<<<dim3(tiles, splits), 128, smem, st>>>(mh, mm, ml, KB, kper, total, np, parts,
-                                                         err, g_wait_cycles, g_stall_producer);
+  if (Xm) {
+    const size_t smem = (size_t)Ring<3>::kBytes + 1024;
+    VIP_TRY(cudaFuncSetAttribute(gram_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    gram_tc_kernel<3><<<dim3(tiles, splits), 128, smem, st>>>(mh, mm, ml, KB, kper, np, parts,
+                                                              err, g_wait_cycles,
+                                                              g_stall_producer);
+  } else {
+    const size_t smem = (size_t)Ring<1>::kBytes + 1024;
+    VIP_TRY(cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    gram_tc_kernel<1><<<dim3(tiles, splits), 128, smem, st>>>(mh, mm, ml, KB, kper, np, parts,
+                                                              err, g_wait_cycles,
+                                                              g_stall_producer);
+  }
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }
@@ -505,7 +526,7 @@ int update_tc_launch(const __nv_bfloat16 *const A[3], const __nv_bfloat16 *const
     if (rc) return rc;
   }
   const int MT = np / 128, NT = dp / 128;
-  const size_t smem = (size_t)GT_STAGES * GT_STAGE_BYTES + 1024;
+  const size_t smem = (size_t)Ring<3>::kBytes + 1024;
   VIP_TRY(cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   VIP_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
