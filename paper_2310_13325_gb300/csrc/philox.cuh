@@ -23,11 +23,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
   return x;
 }
 
-// Two standard normals from two 32-bit words. The radius is formed from a
-// double-precision logarithm so that uniforms near 1 keep their accuracy.
+// Two standard normals from two 32-bit words. With k = ua >> 8, U_a = (k +
+// 1/2) 2^-24 and 1 - U_a = (2^24 - k - 1/2) 2^-24 both have at most 24
+// significant bits, so each is exact in FP32: ln U_a is taken as logf(U_a)
+// below one half and as log1pf(-(1 - U_a)) above, where the argument of logf
+// would lose the small difference from 1. FP32 throughout (FP64 is slow on
+// this GPU); the radius is within a few FP32 ulps of the FP64 value.
 __device__ __forceinline__ float2 box_muller(uint32_t ua, uint32_t ub) {
-  const double Ua = ((double)(ua >> 8) + 0.5) * (1.0 / 16777216.0);
-  const float r = (float)sqrt(-2.0 * log(Ua));
+  const uint32_t k = ua >> 8;
+  const float lg = k >= (1u << 23)
+                       ? log1pf(-((float)((1u << 24) - k) - 0.5f) * (1.0f / 16777216.0f))
+                       : logf(((float)k + 0.5f) * (1.0f / 16777216.0f));
+  const float r = sqrtf(-2.0f * lg);
   const float t = fmaf((float)(ub >> 8), 1.0f / 8388608.0f, 1.0f / 16777216.0f);  // 2 U_b
   float s, c;
   sincospif(t, &s, &c);

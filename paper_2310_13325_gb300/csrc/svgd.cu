@@ -160,17 +160,16 @@ struct Comp {
 // Xc = x - m is formed from the mean held as two floats mh + ml: x - mh
 // exactly (TwoSum), then one rounding of its sum with -ml, which is within
 // 2^-48 |m| of the exact difference. With the matrix-valued kernel (q
-// given) the columns are scaled by sqrt(q_c) in FP64 as before, and 1/q_c
-// and 1/sqrt(q_c) are kept in FP32 for the update, which then needs no FP64
-// division per element.
+// given) that difference is multiplied by sqrt(q_c) rounded to FP32 (so q = 1
+// gives the RBF path's values bit for bit), and 1/q_c and 1/sqrt(q_c) are
+// kept in FP32 for the update, which then needs no FP64 division per element.
 constexpr int kCentreRows = 8;
 __global__ void __launch_bounds__(32 * kCentreRows) centre_kernel(
     const float *__restrict__ X, const float *__restrict__ q, int n, int d, int dp, int np,
     double *mean, float *Xc, __nv_bfloat16 *Xh, __nv_bfloat16 *Xm, __nv_bfloat16 *Xl,
     float *qf, int *nonfinite) {
   __shared__ double part[kCentreRows][32];
-  __shared__ double mcol[32], scol[32];
-  __shared__ float mhc[32], mlc[32];
+  __shared__ float mhc[32], mlc[32], sqc[32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx;
   const bool live = c < d;
@@ -185,12 +184,11 @@ __global__ void __launch_bounds__(32 * kCentreRows) centre_kernel(
     if (!isfinite(t)) atomicOr(nonfinite, 1);   // a NaN or infinity in the column
     const double m = t / n;
     mean[c] = m;
-    mcol[tx] = m;
     const float mh = (float)m;
     mhc[tx] = mh;
     mlc[tx] = (float)(m - (double)mh);
     const double sq = q ? sqrt((double)q[c]) : 1.0;   // Q-metric scale of the column
-    scol[tx] = sq;
+    sqc[tx] = (float)sq;
     if (q) {
       qf[c] = (float)(1.0 / (double)q[c]);
       qf[dp + c] = (float)(1.0 / sq);
@@ -206,19 +204,16 @@ __global__ void __launch_bounds__(32 * kCentreRows) centre_kernel(
     }
     return;
   }
-  const double m = live ? mcol[tx] : 0.0, sq = live ? scol[tx] : 1.0;
   const float nmh = live ? -mhc[tx] : 0.f, ml = live ? mlc[tx] : 0.f;
+  const float sqf = live ? sqc[tx] : 1.f;
   for (int i = ty; i < n; i += kCentreRows) {
     const size_t g = (size_t)i * d + c;
     float xc = 0.f;
     if (live) {
-      if (q) {
-        xc = (float)(((double)X[g] - m) * sq);
-      } else {
-        float e;
-        const float s = two_sum(X[g], nmh, e);
-        xc = __fadd_rn(s, __fsub_rn(e, ml));
-      }
+      float e;
+      const float s = two_sum(X[g], nmh, e);
+      xc = __fadd_rn(s, __fsub_rn(e, ml));
+      if (q) xc = __fmul_rn(xc, sqf);
       Xc[g] = xc;
     }
     if (Xh) {
