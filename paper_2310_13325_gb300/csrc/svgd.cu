@@ -58,6 +58,7 @@ struct SvgdWs {
   int *flag;
   float *K, *rs;
   float *Lk, *Xi;
+  float *L11;               // [32][32] the current Cholesky panel's diagonal factor
   // tensor-core update: A = [Kbar | Lk] and B = [Y | Z]^T as BF16 pieces
   __nv_bfloat16 *Ua[3], *Ub[3];
   float *rcoef;
@@ -107,6 +108,7 @@ static size_t layout(int n, int d, int gp, int stochastic, bool tcu, void *base,
   w.K = cv.take<float>((size_t)n * n);
   w.rs = cv.take<float>(n);
   w.Lk = cv.take<float>(stochastic ? (size_t)n * n : 0);
+  w.L11 = cv.take<float>(stochastic ? 32 * 32 : 0);
   w.Xi = cv.take<float>(stochastic ? (size_t)n * d : 0);
   w.tcu = tcu;
   w.unp = (n + 127) / 128 * 128;
@@ -483,61 +485,87 @@ __global__ void chol_init_kernel(const float *K, int n, float tau, float *A, int
 
 constexpr int CB = 32;   // panel width
 
-__global__ void chol_diag_kernel(float *A, int n, int k0, int *flag) {
+// Panel k0 of the blocked right-looking Cholesky, one warp per block: every
+// block factors the nb x nb diagonal block A11 with lane r holding row r in
+// registers (column c's entries of the other rows arrive by shuffle), in the
+// operation order of a serial right-looking factorisation, then each lane
+// solves one row below the panel, L21 = A21 L11^{-T}, with the row in
+// registers and L11 in shared memory. Other blocks may still be reading A11,
+// so L11 goes to the side buffer L11 (written by block 0), and the
+// trailing-update launch that follows copies it into place; the last panel
+// (no rows below, one block) writes it into A directly. A non-positive pivot
+// is flagged (by block 0) and replaced by 1 so the factorisation ends.
+__global__ void __launch_bounds__(32) chol_panel_kernel(float *A, int n, int k0, float *L11,
+                                                        int *flag) {
   __shared__ float S[CB][CB + 1];
+  const unsigned full = 0xffffffffu;
   const int nb = min(CB, n - k0);
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    S[r][c] = A[(size_t)(k0 + r) * n + k0 + c];
-  }
-  __syncthreads();
-  for (int c = 0; c < nb; ++c) {
-    if (threadIdx.x == 0) {
-      float d = S[c][c];
-      if (!(d > 0.f)) { atomicOr(flag, 1); d = 1.f; }
-      S[c][c] = sqrtf(d);
+  const int l = threadIdx.x;
+  float a[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c)
+    a[c] = (l < nb && c < nb) ? A[(size_t)(k0 + l) * n + k0 + c] : 0.f;
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    if (c < nb) {   // warp-uniform
+      float d = __shfl_sync(full, a[c], c);
+      if (!(d > 0.f)) {
+        if (blockIdx.x == 0 && l == 0) atomicOr(flag, 1);
+        d = 1.f;
+      }
+      const float piv = sqrtf(d);
+      if (l == c) a[c] = piv;
+      const float inv = 1.f / piv;
+      if (l > c) a[c] *= inv;
+#pragma unroll
+      for (int cc = c + 1; cc < CB; ++cc) {
+        const float scc = __shfl_sync(full, a[c], cc);   // scaled entry (cc, c)
+        if (cc < nb && l >= cc) a[cc] = fmaf(-a[c], scc, a[cc]);
+      }
     }
-    __syncthreads();
-    const float inv = 1.f / S[c][c];
-    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) S[r][c] *= inv;
-    __syncthreads();
-    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-      const int r = q / nb, cc = q % nb;
-      if (cc > c && r >= cc) S[r][cc] = fmaf(-S[r][c], S[cc][c], S[r][cc]);
+  }
+#pragma unroll
+  for (int c = 0; c < CB; ++c) S[l][c] = c <= l ? a[c] : 0.f;
+  __syncwarp();
+  const bool last = k0 + nb >= n;
+  if (blockIdx.x == 0 && l < nb) {
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      if (c < nb) {
+        if (last) A[(size_t)(k0 + l) * n + k0 + c] = S[l][c];
+        else L11[l * nb + c] = S[l][c];
+      }
     }
-    __syncthreads();
   }
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    A[(size_t)(k0 + r) * n + k0 + c] = c <= r ? S[r][c] : 0.f;
-  }
-}
-
-// Rows below the panel: L21 = A21 L11^{-T}, one row per thread.
-__global__ void chol_trsm_kernel(float *A, int n, int k0) {
-  __shared__ float L[CB][CB + 1];
-  const int nb = min(CB, n - k0);
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    L[r][c] = A[(size_t)(k0 + r) * n + k0 + c];
-  }
-  __syncthreads();
-  const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = k0 + nb + blockIdx.x * 32 + l;
   if (i >= n) return;
   float x[CB];
-  for (int c = 0; c < nb; ++c) {
-    float v = A[(size_t)i * n + k0 + c];
-    for (int t = 0; t < c; ++t) v = fmaf(-x[t], L[c][t], v);
-    x[c] = v / L[c][c];
-    A[(size_t)i * n + k0 + c] = x[c];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) x[c] = c < nb ? A[(size_t)i * n + k0 + c] : 0.f;
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    if (c < nb) {
+      float v = x[c];
+#pragma unroll
+      for (int t = 0; t < c; ++t) v = fmaf(-x[t], S[c][t], v);
+      x[c] = v / S[c][c];
+    }
   }
+#pragma unroll
+  for (int c = 0; c < CB; ++c)
+    if (c < nb) A[(size_t)i * n + k0 + c] = x[c];
 }
 
-// Trailing update A22 -= L21 L21^T on the lower triangle.
-__global__ void chol_update_kernel(float *A, int n, int k0) {
+// Trailing update A22 -= L21 L21^T on the lower triangle; the first block
+// also copies the panel's diagonal factor L11 into A (no block of this
+// launch reads A11).
+__global__ void chol_update_kernel(float *A, int n, int k0, const float *L11) {
   __shared__ float Ai[CB][65], Aj[CB][65];
   const int nb = min(CB, n - k0);
   const int k1 = k0 + nb;
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x)
+      A[(size_t)(k0 + q / nb) * n + k0 + q % nb] = L11[q];
   const int i0 = k1 + blockIdx.y * 64, j0 = k1 + blockIdx.x * 64;
   if (j0 > i0 + 63) return;
   for (int q = threadIdx.x; q < 64 * CB; q += 256) {
@@ -860,14 +888,13 @@ static int run_svgd(float *X, const float *G, float gscale, const float *q, int 
         w.K, n, (float)tau, w.Lk, w.flag);
     VIP_CHECK_LAUNCH();
     for (int k0 = 0; k0 < n; k0 += CB) {
-      chol_diag_kernel<<<1, 256, 0, st>>>(w.Lk, n, k0, w.flag);
-      VIP_CHECK_LAUNCH();
       const int rest = n - k0 - std::min(CB, n - k0);
+      chol_panel_kernel<<<std::max(1, idiv_up(rest, 32)), 32, 0, st>>>(w.Lk, n, k0, w.L11,
+                                                                      w.flag);
+      VIP_CHECK_LAUNCH();
       if (rest > 0) {
-        chol_trsm_kernel<<<idiv_up(rest, 128), 128, 0, st>>>(w.Lk, n, k0);
-        VIP_CHECK_LAUNCH();
         const int nb64 = idiv_up(rest, 64);
-        chol_update_kernel<<<dim3(nb64, nb64), 256, 0, st>>>(w.Lk, n, k0);
+        chol_update_kernel<<<dim3(nb64, nb64), 256, 0, st>>>(w.Lk, n, k0, w.L11);
         VIP_CHECK_LAUNCH();
       }
     }
