@@ -956,7 +956,9 @@ def main():
         line["e2e"] = {"value": job_value(P, ws_, e2e_max), "unit": UNIT,
                        "h2d_bytes_per_step": res["h2d_bytes"],
                        "d2h_bytes_per_step": res["d2h_bytes"]}
-    if not args.no_cpu_baseline:
+    # the FP64 oracle on the host cores: rank 0 of a single-GPU run only (a
+    # multi-GPU run would hold every GPU while it runs)
+    if not args.no_cpu_baseline and ws_ == 1:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line))
     if ws_ > 1:
