@@ -152,6 +152,22 @@ def test_ssvgd_step_injected_noise_matches_oracle():
     assert rel(Xt.cpu().numpy() - X, X_ref - X) <= 1e-5
 
 
+@pytest.mark.parametrize("n", [31, 32, 33, 65, 97])
+def test_ssvgd_cholesky_panels_match_oracle(n):
+    # the blocked Cholesky of Kbar + tau I works in 32-wide panels: one short
+    # panel, exactly one, one plus a single row, several with a ragged last
+    # one. The noise term sqrt(2 eps / n) Lk Xi of the move carries the factor.
+    X, G = _unit_case(n, 1000, seed=40 + n)
+    xi = np.random.default_rng(50 + n).standard_normal(X.shape).astype(np.float32)
+    xi = xi.astype(np.float64)
+    Xt = _t(X)
+    eps = 0.05
+    _, _, tau = vg.ssvgd_step(Xt, _t(G), eps, seed=0, it=0, xi=_t(xi))
+    X_ref, _, tau_ref = osvgd.ssvgd_step(X, G, eps, xi)
+    assert tau.item() == pytest.approx(tau_ref)
+    assert rel(Xt.cpu().numpy() - X, X_ref - X) <= 1e-5
+
+
 def test_ssvgd_step_philox_noise_matches_oracle_stream():
     X, G = _unit_case(12, 2049, seed=10)
     seed, it = 3, 17
