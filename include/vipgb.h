@@ -340,7 +340,8 @@ int  ssvgd_step_q(float *X, const float *G, float gscale, const float *q, int n,
                   const float *xi, double *tau_used, vip_stream_t stream);
 
 /* q_c = 1 / Var_j(X[j][c]) for the particles X [n][d] (device, FP32 in,
- * FP64 two-pass population variance), 1 where the variance is zero; the
+ * two-pass population variance, FP64-class: compensated FP32 sums per
+ * thread, FP64 across threads), 1 where the variance is zero; the
  * choice of Q the Discussion section gives. q: device [d], caller-owned. */
 int  svgd_inverse_variance(const float *X, int n, int d, float *q,
                            vip_stream_t stream);

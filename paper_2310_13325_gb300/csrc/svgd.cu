@@ -37,6 +37,7 @@
 #include "gram.cuh"
 #include "philox.cuh"
 
+#include <math_constants.h>
 #include <cmath>
 #include <mutex>
 
@@ -237,21 +238,65 @@ __global__ void __launch_bounds__(32 * kCentreRows) centre_kernel(
     }
 }
 
-// q_c = 1 / Var_j(x_jc), the population variance over the particles in
-// FP64 (two passes), and 1 where the variance is zero.
-__global__ void inverse_variance_kernel(const float *__restrict__ X, int n, int d, float *q) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d) return;
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * d + c];
-  const double m = s / n;
-  double v = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double t = (double)X[(size_t)i * d + c] - m;
-    v += t * t;
+// q_c = 1 / Var_j(x_jc), the population variance over the particles, and 1
+// where the variance is zero (every particle equal in the column, found
+// from the column's minimum and maximum, exactly). A block owns 32 columns
+// and its 8 warps interleaved rows, as in centre_kernel: the mean from
+// compensated FP32 sums (FP64 across the warps, in a fixed order), then the
+// squared deviations x - m (formed as in centre_kernel) summed the same way.
+__global__ void __launch_bounds__(32 * kCentreRows) inverse_variance_kernel(
+    const float *__restrict__ X, int n, int d, float *q) {
+  __shared__ double part[kCentreRows][32];
+  __shared__ float mhc[32], mlc[32];
+  __shared__ float lo_s[kCentreRows][32], hi_s[kCentreRows][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
+  const bool live = c < d;
+  Comp acc;
+  float lo = CUDART_INF_F, hi = -CUDART_INF_F;
+  if (live)
+    for (int i = ty; i < n; i += kCentreRows) {
+      const float x = X[(size_t)i * d + c];
+      acc.add(x);
+      lo = fminf(lo, x);
+      hi = fmaxf(hi, x);
+    }
+  part[ty][tx] = acc.value();
+  lo_s[ty][tx] = lo;
+  hi_s[ty][tx] = hi;
+  __syncthreads();
+  if (ty == 0 && live) {
+    double t = 0.0;
+    for (int r = 0; r < kCentreRows; ++r) t += part[r][tx];
+    const double m = t / n;
+    const float mh = (float)m;
+    mhc[tx] = mh;
+    mlc[tx] = (float)(m - (double)mh);
   }
-  v /= n;
-  q[c] = v > 0.0 ? (float)(1.0 / v) : 1.f;
+  __syncthreads();
+  Comp sq;
+  if (live) {
+    const float nmh = -mhc[tx], ml = mlc[tx];
+    for (int i = ty; i < n; i += kCentreRows) {
+      float e;
+      const float s = two_sum(X[(size_t)i * d + c], nmh, e);
+      sq.add_sq(__fadd_rn(s, __fsub_rn(e, ml)));
+    }
+  }
+  __syncthreads();   // every thread has read part[][] of the first pass
+  part[ty][tx] = sq.value();
+  __syncthreads();
+  if (ty == 0 && live) {
+    double v = 0.0;
+    float cl = lo_s[0][tx], ch = hi_s[0][tx];
+    for (int r = 0; r < kCentreRows; ++r) {
+      v += part[r][tx];
+      cl = fminf(cl, lo_s[r][tx]);
+      ch = fmaxf(ch, hi_s[r][tx]);
+    }
+    v /= n;
+    q[c] = (cl == ch || !(v > 0.0)) ? 1.f : (float)(1.0 / v);
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -1034,7 +1079,7 @@ int ssvgd_step_q(float *X, const float *G, float gscale, const float *q, int n, 
 
 int svgd_inverse_variance(const float *X, int n, int d, float *q, vip_stream_t stream) {
   if (!X || !q || n < 1 || d < 1) return VIP_ERR_ARG;
-  inverse_variance_kernel<<<idiv_up(d, 128), 128, 0, stream>>>(X, n, d, q);
+  inverse_variance_kernel<<<idiv_up(d, 32), 32 * kCentreRows, 0, stream>>>(X, n, d, q);
   VIP_CHECK_LAUNCH();
   return VIP_OK;
 }

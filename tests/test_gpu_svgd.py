@@ -226,9 +226,13 @@ def _scaled_case(n, d, seed):
     return X, G
 
 
-@pytest.mark.parametrize("n,d", [(9, 4096), (2, 3), (130, 1000)])
-def test_inverse_variance_matches_oracle(n, d):
+@pytest.mark.parametrize("n,d,offset", [(9, 4096, 0.0), (2, 3, 0.0), (130, 1000, 0.0),
+                                        (600, 2000, 3000.0)])
+def test_inverse_variance_matches_oracle(n, d, offset):
+    # offset: velocity-like coordinates, a spread of 0.1 to 20 on a mean of
+    # 3000, where the deviations are small against the values
     X, _ = _scaled_case(n, d, seed=n)
+    X = (X + offset).astype(np.float32).astype(np.float64)
     X[:, 0] = X[0, 0]                     # a coordinate without spread: q = 1
     q = vg.svgd_inverse_variance(_t(X)).cpu().numpy()
     ref = osvgd.inverse_variance(X)
