@@ -63,6 +63,12 @@ void vip_clear_error(void);
  *   J = 1/2 sum_{s,r,n} ((d - d_obs) / sigma)^2,
  * and gradients are those of the exact discrete adjoint of the recurrence,
  * folded from the padded grid onto the physical cells.
+ *
+ * Batches: fwi_forward, fwi_gradient, fwi_gradient_sources and fwi_adjoint
+ * take P >= 0 models. P = 0 is an empty batch (a rank or minibatch that holds
+ * no particles): the other arguments are still checked, the P-sized pointers
+ * may be NULL, and the call returns VIP_OK without any device work. P < 0 is
+ * VIP_ERR_ARG.
  * ====================================================================== */
 
 typedef struct {

@@ -966,8 +966,10 @@ static int run_plain(fwi_ctx *c, int mode, const float *v, int P, const float *d
   return VIP_OK;
 }
 
+// P = 0 is an empty batch: the entry points check their other arguments and
+// return VIP_OK without touching the device (pointers may then be NULL).
 static int check_call(fwi_ctx *c, const float *v, int P) {
-  if (!c || !v || P < 1) return VIP_ERR_ARG;
+  if (!c || P < 0 || (P > 0 && !v)) return VIP_ERR_ARG;
   return VIP_OK;
 }
 
@@ -1155,7 +1157,8 @@ int fwi_query_plan(fwi_ctx *c, int P, int precision, int *plan_out, size_t *byte
 
 int fwi_forward(fwi_ctx *c, const float *v, int P, float *seis, vip_stream_t stream) {
   int rc = check_call(c, v, P);
-  if (rc || !seis) return rc ? rc : VIP_ERR_ARG;
+  if (rc || (P > 0 && !seis)) return rc ? rc : VIP_ERR_ARG;
+  if (P == 0) return VIP_OK;
   if (c->mode == FWI_MODE_PLAIN)
     return run_plain(c, WM_FORWARD, v, P, nullptr, nullptr, 1.f, nullptr, nullptr, seis, stream);
   return run_batched(c, WM_FORWARD, v, P, nullptr, nullptr, 1.f, nullptr, nullptr, seis,
@@ -1166,10 +1169,12 @@ int fwi_gradient(fwi_ctx *c, const float *v, int P, const float *dobs, double si
                  double *misfit, float *grad, int precision, vip_stream_t stream) {
   int rc = check_call(c, v, P);
   if (rc) return rc;
-  if (!dobs || !grad || !(sigma > 0) || precision < FWI_FP32 || precision > FWI_CKPT_FP16)
+  if ((P > 0 && (!dobs || !grad)) || !(sigma > 0) || precision < FWI_FP32 ||
+      precision > FWI_CKPT_FP16)
     return VIP_ERR_ARG;
+  if (c->mode == FWI_MODE_PLAIN && precision != FWI_FP32) return VIP_ERR_ARG;
+  if (P == 0) return VIP_OK;
   if (c->mode == FWI_MODE_PLAIN) {
-    if (precision != FWI_FP32) return VIP_ERR_ARG;
     if (P * c->S > 4096) return VIP_ERR_ARG;
     return run_plain(c, WM_GRADIENT, v, P, dobs, nullptr, sigma, misfit, grad, nullptr, stream);
   }
@@ -1182,12 +1187,13 @@ int fwi_gradient_sources(fwi_ctx *c, const float *v, int P, const float *dobs, d
                          int precision, vip_stream_t stream) {
   int rc = check_call(c, v, P);
   if (rc) return rc;
-  if (!dobs || !grad || !sources || nb < 1 || nb > c->S || !(sigma > 0) ||
+  if ((P > 0 && (!dobs || !grad)) || !sources || nb < 1 || nb > c->S || !(sigma > 0) ||
       precision < FWI_FP32 || precision > FWI_CKPT_FP16)
     return VIP_ERR_ARG;
   for (int k = 0; k < nb; ++k)
     if (sources[k] < 0 || sources[k] >= c->S) return VIP_ERR_ARG;
   if (c->mode == FWI_MODE_PLAIN) return VIP_ERR_UNSUPPORTED;
+  if (P == 0) return VIP_OK;
   const size_t trace = (size_t)c->R * c->N;
   if (!c->d_sub_z) {
     // all three buffers or none: a partial allocation is released, so a later
@@ -1227,9 +1233,11 @@ int fwi_adjoint(fwi_ctx *c, const float *v, int P, const float *dseis, float *gr
                 int precision, vip_stream_t stream) {
   int rc = check_call(c, v, P);
   if (rc) return rc;
-  if (!dseis || !grad || precision < FWI_FP32 || precision > FWI_CKPT_FP16) return VIP_ERR_ARG;
+  if ((P > 0 && (!dseis || !grad)) || precision < FWI_FP32 || precision > FWI_CKPT_FP16)
+    return VIP_ERR_ARG;
+  if (c->mode == FWI_MODE_PLAIN && precision != FWI_FP32) return VIP_ERR_ARG;
+  if (P == 0) return VIP_OK;
   if (c->mode == FWI_MODE_PLAIN) {
-    if (precision != FWI_FP32) return VIP_ERR_ARG;
     return run_plain(c, WM_ADJOINT, v, P, nullptr, dseis, 1.f, nullptr, grad, nullptr, stream);
   }
   return run_batched(c, WM_ADJOINT, v, P, nullptr, dseis, 1.f, nullptr, grad, nullptr, precision,

@@ -283,6 +283,42 @@ def test_single_particle_and_source_split_work_items():
     assert plan["sources_per_item"] >= 1
 
 
+def test_empty_batch_is_a_no_op():
+    """P = 0 (a rank or a minibatch that holds no particles) returns VIP_OK with
+    empty results from every FWI entry point, the P-sized pointers may be NULL,
+    the other arguments are still checked, and the context computes normally
+    afterwards."""
+    import ctypes
+    cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = cfg1_case(2)
+    J_ref, G_ref = cfg1_oracle_gradients(2)
+    fwi = vg.Fwi.from_config(cfg, geo)
+    v0 = torch.empty((0, cfg.nz, cfg.nx), device=DEV)
+    dobs = _t(d_obs)
+    assert tuple(fwi.forward(v0).shape) == (0, g.nsrc, g.nrec, g.nt)
+    J, G = fwi.gradient(v0, dobs, sigma)
+    assert tuple(J.shape) == (0,) and tuple(G.shape) == (0, cfg.nz, cfg.nx)
+    J, G = fwi.gradient(v0, dobs, sigma, sources=[0, 2])
+    assert tuple(J.shape) == (0,) and tuple(G.shape) == (0, cfg.nz, cfg.nx)
+    dseis = torch.empty((0, g.nsrc, g.nrec, g.nt), device=DEV)
+    assert tuple(fwi.adjoint(v0, dseis).shape) == (0, cfg.nz, cfg.nx)
+    L, h = fwi._L, fwi._h
+    src = (ctypes.c_int * 1)(1)
+    assert L.fwi_forward(h, None, 0, None, None) == 0
+    assert L.fwi_gradient(h, None, 0, None, sigma, None, None, 0, None) == 0
+    assert L.fwi_gradient_sources(h, None, 0, None, sigma, ctypes.cast(src, ctypes.c_void_p), 1,
+                                  None, None, 0, None) == 0
+    assert L.fwi_adjoint(h, None, 0, None, None, 0, None) == 0
+    assert L.fwi_forward(h, None, -1, None, None) == -1
+    assert L.fwi_gradient(h, None, 0, None, -1.0, None, None, 0, None) == -1
+    assert L.fwi_gradient(h, None, 0, None, sigma, None, None, 7, None) == -1
+    assert L.fwi_gradient_sources(h, None, 0, None, sigma, None, 1, None, None, 0, None) == -1
+    torch.cuda.synchronize()
+    J, G = fwi.gradient(_t(V), dobs, sigma)
+    assert rel(G.reshape(2, -1).cpu().numpy(), G_ref) <= 1e-5
+    assert np.all(np.abs(J.cpu().numpy() - J_ref) <= _cfg1_jtol() * J_ref)
+    assert fwi.last_status() == 0
+
+
 def test_full_size_cfg3_sampled_traces_and_gradient_direction():
     """cfg3 grid (120 x 300, 2000 steps, 200 receivers) in the launch shape the
     benchmark uses: traces of sampled (particle, source) pairs against the
