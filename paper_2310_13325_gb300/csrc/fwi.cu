@@ -95,6 +95,7 @@ struct fwi_ctx {
   // plain-mode buffers
   float *pl_W = nullptr, *pl_a = nullptr, *pl_Gm = nullptr, *pl_gz = nullptr, *pl_gx = nullptr;
   int *pl_recmap = nullptr;
+  bool pl_ready = false;   // every plain-mode buffer allocated and filled
   // source minibatches (fwi_gradient_sources): the chosen sources' positions
   // and observed traces, gathered in front of a call, sized for all sources
   int *d_sub_z = nullptr, *d_sub_x = nullptr;
@@ -174,26 +175,35 @@ static int get_tables(fwi_ctx *c, int Q, int V, Tables **out) {
     perm[i] = r;
     roff[i] = (c->rec_z[r] % t.Hb) * PX + 4 + c->rec_x[r];
   }
-  VIP_TRY(cudaMalloc(&t.gz, gz.size() * 4));
-  VIP_TRY(cudaMalloc(&t.gx, gx.size() * 4));
-  VIP_TRY(cudaMalloc(&t.rmask, mask.size() * 8));
-  VIP_TRY(cudaMalloc(&t.rbase, base.size() * 4));
-  VIP_TRY(cudaMalloc(&t.rperm, perm.size() * 4));
-  VIP_TRY(cudaMalloc(&t.roff, roff.size() * 4));
   std::vector<int> bstart(Q + 1, 0);
   for (int i = 0; i < c->R; ++i) bstart[order[i][0] / 64 / t.ntask_pad + 1]++;
   for (int b = 0; b < Q; ++b) {
     t.rmax = std::max(t.rmax, bstart[b + 1]);
     bstart[b + 1] += bstart[b];
   }
-  VIP_TRY(cudaMalloc(&t.rbstart, bstart.size() * 4));
-  VIP_TRY(cudaMemcpy(t.rbstart, bstart.data(), bstart.size() * 4, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.gz, gz.data(), gz.size() * 4, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.gx, gx.data(), gx.size() * 4, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.rmask, mask.data(), mask.size() * 8, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.rbase, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.rperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
-  VIP_TRY(cudaMemcpy(t.roff, roff.data(), roff.size() * 4, cudaMemcpyHostToDevice));
+  // device copies, all or none (a failure part way frees what was made)
+  auto upload = [&]() -> int {
+    VIP_TRY(cudaMalloc(&t.gz, gz.size() * 4));
+    VIP_TRY(cudaMalloc(&t.gx, gx.size() * 4));
+    VIP_TRY(cudaMalloc(&t.rmask, mask.size() * 8));
+    VIP_TRY(cudaMalloc(&t.rbase, base.size() * 4));
+    VIP_TRY(cudaMalloc(&t.rperm, perm.size() * 4));
+    VIP_TRY(cudaMalloc(&t.roff, roff.size() * 4));
+    VIP_TRY(cudaMalloc(&t.rbstart, bstart.size() * 4));
+    VIP_TRY(cudaMemcpy(t.rbstart, bstart.data(), bstart.size() * 4, cudaMemcpyHostToDevice));
+    VIP_TRY(cudaMemcpy(t.gz, gz.data(), gz.size() * 4, cudaMemcpyHostToDevice));
+    VIP_TRY(cudaMemcpy(t.gx, gx.data(), gx.size() * 4, cudaMemcpyHostToDevice));
+    VIP_TRY(cudaMemcpy(t.rmask, mask.data(), mask.size() * 8, cudaMemcpyHostToDevice));
+    VIP_TRY(cudaMemcpy(t.rbase, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
+    VIP_TRY(cudaMemcpy(t.rperm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice));
+    VIP_TRY(cudaMemcpy(t.roff, roff.data(), roff.size() * 4, cudaMemcpyHostToDevice));
+    return VIP_OK;
+  };
+  if (const int rc = upload()) {
+    cudaFree(t.gz); cudaFree(t.gx); cudaFree(t.rmask); cudaFree(t.rbase); cudaFree(t.rperm);
+    cudaFree(t.roff); cudaFree(t.rbstart);
+    return rc;
+  }
   c->tables.push_back(t);
   *out = &c->tables.back();
   return VIP_OK;
@@ -819,8 +829,16 @@ __global__ void plain_fold(const float *Gm, const float *v, int nz, int nx, int 
   grad[q] = (float)(acc * 2.0 / ((double)v[q] * (double)dx2));
 }
 
-static int ensure_plain(fwi_ctx *c) {
-  if (c->pl_W) return VIP_OK;
+static void free_plain(fwi_ctx *c) {
+  cudaFree(c->pl_W); cudaFree(c->pl_a); cudaFree(c->pl_Gm); cudaFree(c->pl_gz);
+  cudaFree(c->pl_gx); cudaFree(c->pl_recmap); cudaFree(c->pl_J);
+  c->pl_W = c->pl_a = c->pl_Gm = c->pl_gz = c->pl_gx = nullptr;
+  c->pl_recmap = nullptr;
+  c->pl_J = nullptr;
+  c->pl_ready = false;
+}
+
+static int alloc_plain(fwi_ctx *c) {
   const size_t C = (size_t)c->NZ * c->NX;
   VIP_TRY(cudaMalloc(&c->pl_W, C * 4));
   VIP_TRY(cudaMalloc(&c->pl_a, 2 * C * 4));
@@ -842,6 +860,20 @@ static int ensure_plain(fwi_ctx *c) {
   VIP_TRY(cudaMemcpy(c->pl_gz, gz.data(), c->NZ * 4, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(c->pl_gx, gx.data(), c->NX * 4, cudaMemcpyHostToDevice));
   VIP_TRY(cudaMemcpy(c->pl_recmap, rm.data(), C * 4, cudaMemcpyHostToDevice));
+  return VIP_OK;
+}
+
+// The plain-mode buffers are made on first use, all or none: a failure part
+// way releases what was allocated, so a later call retries instead of
+// launching on a missing buffer.
+static int ensure_plain(fwi_ctx *c) {
+  if (c->pl_ready) return VIP_OK;
+  const int rc = alloc_plain(c);
+  if (rc) {
+    free_plain(c);
+    return rc;
+  }
+  c->pl_ready = true;
   return VIP_OK;
 }
 
@@ -1077,8 +1109,7 @@ void fwi_destroy(fwi_ctx *c) {
   }
   cudaFree(c->scratch);
   cudaFree(c->d_wavelet); cudaFree(c->d_src_z); cudaFree(c->d_src_x); cudaFree(c->d_status);
-  cudaFree(c->pl_W); cudaFree(c->pl_a); cudaFree(c->pl_Gm); cudaFree(c->pl_gz);
-  cudaFree(c->pl_gx); cudaFree(c->pl_recmap); cudaFree(c->pl_J);
+  vip::free_plain(c);
   cudaFree(c->d_sub_z); cudaFree(c->d_sub_x); cudaFree(c->d_sub_dobs);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->fill_stream) cudaStreamDestroy(c->fill_stream);
