@@ -418,9 +418,9 @@ def wave_roofline(cell_updates, t_ms, hbm, hbm_src, peaks):
     fwi_gradient, 99.9 % of the step's device time). It keeps the wavefields in
     shared memory, so DRAM carries only the stored snapshots; what bounds it is
     instruction issue on the FP32 pipe. Reported against the FP32 lane peak
-    (152 SMs x 128 lanes x the maximum SM clock), with the survey's streaming
-    count (16 B per cell update) and the measured DRAM traffic against the HBM
-    peak beside it."""
+    (152 SMs x 128 lanes x the maximum SM clock), with the streaming count of
+    a stencil that reads its fields from DRAM (16 B per cell update) and the
+    measured DRAM traffic against the HBM peak beside it."""
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
     lane_peak = 152 * 128 * sm_mhz * 1e6 / 1e12               # T lane-op/s
     achieved = LANE_OPS_PER_CELL_UPDATE * cell_updates / (t_ms * 1e-3) / 1e12
@@ -437,7 +437,7 @@ def wave_roofline(cell_updates, t_ms, hbm, hbm_src, peaks):
                     "streaming_equivalent": equiv, "streaming_equivalent_frac": equiv / hbm,
                     "dram": traffic / (t_ms * 1e-3) / 1e9 if traffic else None,
                     "dram_frac": traffic / (t_ms * 1e-3) / 1e9 / hbm if traffic else None,
-                    "note": "streaming_equivalent counts the survey's 16 B per cell update "
+                    "note": "streaming_equivalent counts 16 B per cell update "
                             "(read a^n, a^{n-1}, w; write a^{n+1}) although the fields stay "
                             "on chip; dram is the ncu-measured traffic (stored snapshots) "
                             "scaled by cell updates"},
