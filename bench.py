@@ -869,12 +869,36 @@ def run_update(args, torch):
         ev.append((a, b))
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    print(json.dumps({"metric": "%s time" % ("ssvgd_step" if args.stochastic else "svgd_step"),
-                      "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
-                      "warmup": max(args.warmup, 3), "ms_per_step": ms,
-                      "higher_is_better": False, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "%d particles x %d coordinates, three-piece BF16 "
-                                             "Gram, tensor-core update" % (n, d)}}))
+    line = {"metric": "%s time" % ("ssvgd_step" if args.stochastic else "svgd_step"),
+            "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d particles x %d coordinates, three-piece BF16 "
+                                   "Gram, tensor-core update" % (n, d)}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = update_cpu_baseline(n, d, args.stochastic)
+    print(json.dumps(line))
+
+
+def update_cpu_baseline(n, d, stochastic):
+    """The FP64 oracle's svgd_step / ssvgd_step as it stands, in this process,
+    on a bounded sample: ns = min(n, 150) seeded particles of the same d. Its
+    work grows as n^2 d (the pairwise distances, taken row by row, and the
+    kernel products), so the time is scaled by (n / ns)^2."""
+    from oracle import svgd as osvgd
+    ns = min(n, 150)
+    rng = np.random.default_rng(7)
+    X, G, xi = (rng.standard_normal((ns, d)) for _ in range(3))
+    t0 = time.perf_counter()
+    if stochastic:
+        osvgd.ssvgd_step(X, G, 1e-3, xi)
+    else:
+        osvgd.svgd_step(X, G, 1e-3)
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3 * (n / ns) ** 2, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": "one oracle %s on %d x %d particles (%.1f s), scaled by (%d / %d)^2; "
+                      "one process (its row loops on one core, K @ G on the BLAS threads)"
+                      % ("ssvgd_step" if stochastic else "svgd_step", ns, d, dt, n, ns)}
 
 
 def reduce_over_ranks(t_ms, e2e_ms, device):
