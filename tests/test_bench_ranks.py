@@ -2,7 +2,7 @@
 the slowest rank's time, and the job value counts every rank's particles.
 (The ranks' particles are coupled by the update through one all-gather per
 iteration, covered by tests/test_sharded.py; this file covers the timing
-reduction and the launch accounting.)"""
+reduction, the launch accounting and the oracle leg of the update workload.)"""
 import os
 import socket
 
@@ -58,3 +58,15 @@ def test_launch_count_of_a_gradient_plan():
     fill = {"cluster_ctas": 2, "rows_per_thread": 8, "threads": 288, "clusters": 4}
     assert bench.fwi_gradient_launches({"sources_per_item": 2, "fill": fill}, 20) == 4
     assert bench.SVGD_STEP_LAUNCHES == 20
+
+
+def test_update_baseline_is_the_oracle_on_a_scaled_sample():
+    # the oracle's update on min(n, 150) particles, its time scaled by (n / ns)^2
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    small = bench.update_cpu_baseline(12, 64, False)
+    assert small["kind"] == "oracle" and small["unit"] == "ms" and small["value"] > 0
+    assert "12 x 64" in small["sample"] and "(12 / 12)^2" in small["sample"]
+    big = bench.update_cpu_baseline(300, 8, True)
+    assert "ssvgd_step on 150 x 8" in big["sample"] and "(300 / 150)^2" in big["sample"]
