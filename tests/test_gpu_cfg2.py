@@ -3,7 +3,8 @@ steps at 1 ms) with restart checkpoints every 50 steps and recomputation:
 
 * the autograd backward of the seismogram map (FwiSeis, i.e. fwi_adjoint)
   for the Gaussian misfit equals the FP64 oracle gradient (rel-L2 <= 1e-5) and
-  fwi_gradient;
+  fwi_gradient, whose misfit is held to the tolerance derived from the trace
+  bound (misfit_tolerance);
 * linearisation dot product: <J dv, r> (central difference of fwi_forward,
   h = 0.25 along a smooth dv, r the model's own traces) equals <dv, J^T r>
   (fwi_adjoint) to 2e-3;
@@ -22,7 +23,7 @@ torch = pytest.importorskip("torch")
 import synth
 from oracle import fwi as ofwi
 import paper_2310_13325_gb300 as vg
-from gpu_common import problem, rel
+from gpu_common import misfit_tolerance, oracle_gradients, problem, rel
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -38,12 +39,13 @@ def case():
     build.build()
     cfg = synth.config("cfg2")
     cfg, geo, g, v_true, V, d_obs, sigma, lo, hi = problem(cfg, 1)
-    J_ref, G_ref = ofwi.gradients(V, g, d_obs, sigma)
-    return cfg, geo, g, V, d_obs, sigma, J_ref, G_ref
+    J_ref, G_ref, _, traces = oracle_gradients(g, V, range(g.nsrc), d_obs, sigma)
+    tr = np.stack([traces[(0, s)] for s in range(g.nsrc)])[None]
+    return cfg, geo, g, V, d_obs, sigma, J_ref, G_ref, misfit_tolerance(tr, d_obs)
 
 
 def test_autograd_with_checkpoints_matches_oracle(case):
-    cfg, geo, g, V, d_obs, sigma, J_ref, G_ref = case
+    cfg, geo, g, V, d_obs, sigma, J_ref, G_ref, jtol = case
     fwi = vg.Fwi.from_config(cfg, geo)
     plan1 = fwi.query_plan(1)
     fwi.set_mode(vg.FWI_MODE_BATCHED, cfg.ckpt_every)
@@ -61,11 +63,12 @@ def test_autograd_with_checkpoints_matches_oracle(case):
     J, G = fwi.gradient(_t(V), _t(d_obs), sigma)
     assert rel(G.reshape(-1).cpu().numpy(), G_ref[0]) <= 1e-5
     assert rel(g_auto, G.reshape(-1).cpu().numpy()) <= 1e-6
-    assert abs(J.item() - J_ref[0]) <= 3e-5 * J_ref[0]
+    print("misfit rel. error %.2e, tolerance %.2e" % (abs(J.item() - J_ref[0]) / J_ref[0], jtol))
+    assert abs(J.item() - J_ref[0]) <= jtol * J_ref[0]
 
 
 def test_linearisation_dot_product(case):
-    cfg, geo, g, V, d_obs, sigma, J_ref, G_ref = case
+    cfg, geo, g, V, d_obs, sigma, J_ref, G_ref, jtol = case
     fwi = vg.Fwi.from_config(cfg, geo)
     fwi.set_mode(vg.FWI_MODE_BATCHED, cfg.ckpt_every)
     v = _t(V).reshape(1, cfg.nz, cfg.nx)

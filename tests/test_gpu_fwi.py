@@ -6,9 +6,11 @@ residuals. The misfit (Eq. 26) rounds each residual to FP32 once (2^-24), sums
 the squares of each receiver's residuals in FP32 over blocks of 16 steps
 (relative error <= 16 * 2^-24 ~ 1e-6) and accumulates those block sums per
 receiver in FP64, then over receivers in a fixed order: the reduction is held
-to 4e-6 against an FP64 sum of the same GPU traces, and its value against the oracle to a tolerance derived per case
-from the trace tolerance: dJ/J ~ 2 <r, dd> / |r|^2 <= 2 (|d| / |r|) rel(d) +
-4e-6, |d| / |r| measured on the oracle's traces (misfit_tolerance).
+to its rounding bound, 18 * 2^-24 ~ 1.07e-6 (MISFIT_REDUCTION_TOL = 1.1e-6),
+against an FP64 sum of the same GPU traces, and its value against the oracle to
+a tolerance derived per case from the trace tolerance: dJ/J ~ 2 <r, dd> / |r|^2
+<= 2 (|d| / |r|) rel(d) + 1.1e-6, |d| / |r| measured on the oracle's traces
+(misfit_tolerance).
 Reduced-precision snapshots are measured and held to the bounds stated with
 each test.
 """
@@ -20,8 +22,8 @@ torch = pytest.importorskip("torch")
 import synth
 from oracle import fwi as ofwi
 import paper_2310_13325_gb300 as vg
-from gpu_common import (cfg1_case, cfg1_oracle_gradients, misfit_tolerance, odd_config,
-                        oracle_gradients, problem, rel)
+from gpu_common import (MISFIT_REDUCTION_TOL, cfg1_case, cfg1_oracle_gradients,
+                        misfit_tolerance, odd_config, oracle_gradients, problem, rel)
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -70,7 +72,7 @@ def test_gradient_and_misfit_match_oracle_cfg1():
     tr = fwi.forward(_t(V)).double().cpu().numpy()
     J_host = 0.5 * ((tr - d_obs.astype(np.float32)[None]) ** 2).sum(axis=(1, 2, 3)) / sigma ** 2
     print("misfit reduction rel. error:", np.abs(J - J_host) / J_host)
-    assert np.all(np.abs(J - J_host) <= 4e-6 * J_host), (J, J_host)
+    assert np.all(np.abs(J - J_host) <= MISFIT_REDUCTION_TOL * J_host), (J, J_host)
 
 
 def test_plain_loop_equals_batched_bit_for_bit():
@@ -87,9 +89,11 @@ def test_plain_loop_equals_batched_bit_for_bit():
     Sp = fwi.forward(Vt)
     assert torch.equal(Sb, Sp)
     assert torch.equal(Gb, Gp)
-    # same FP32 residuals; the batched kernel sums their squares in FP32 over
-    # 16 steps per receiver before the FP64 accumulation (bound 16 * 2^-24)
-    assert torch.allclose(Jb, Jp, rtol=4e-6, atol=0)
+    # same FP32 residuals, whose squares the plain loop adds in FP64; the
+    # batched kernel sums them in FP32 over 16 steps per receiver before the
+    # FP64 accumulation (bound 16 * 2^-24, within MISFIT_REDUCTION_TOL)
+    print("batched / plain misfit rel. difference:", ((Jb - Jp).abs() / Jp).tolist())
+    assert torch.allclose(Jb, Jp, rtol=MISFIT_REDUCTION_TOL, atol=0)
 
 
 @pytest.mark.parametrize("K", [7, 50])
